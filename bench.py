@@ -1,0 +1,344 @@
+"""Benchmark: synaptic events/s of the column-network step on GB300.
+
+A bench step is one 1 ms simulation step (neuron update + spike delivery) of
+the 24x24-column network (714 240 neurons, 885.7 M synapses, FP32 weights,
+seed 2) unless --workload names another one.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl ours|reference] [--no-extra]
+
+N > 1 runs N independent replicas (one network per GPU, seed + rank), launched
+with torch.distributed.run; rank 0 prints the whole-job line.
+--impl reference times the CPU oracle on a bounded sample of the workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1511_09325_gb300 import workloads as W  # noqa: E402
+
+METRIC = "synaptic events/s and wall-s per model-s on 1 GB300; FP16-weight vs plain FP32 path"
+UNIT = "events/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--workload", default="cols24x24_f32w")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 96x96 FP16-vs-FP32 comparison")
+    ap.add_argument("--profile-steps", type=int, default=2000)
+    ap.add_argument("--e2e-steps", type=int, default=1000)
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic(workload, kernel):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if any."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            t = json.load(f)
+        return t.get(workload, {}).get(kernel)
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.out = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or (self.uuid and not self.uuid.startswith(f[0][:12]) and self.uuid not in f[0]):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _cpu_baseline(workload, seconds_target=15.0):
+    """The oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+
+    cfg = W.WORKLOADS[workload]
+    n, s = W.neuron_params(), W.synapse_params()
+    p = oracle.make_params(cfg["grid_w"], cfg["grid_h"], n, s, cfg["seed"])
+    mode = cfg["precision"]
+    oracle.build()
+    steps = 1
+    while True:
+        t0 = time.perf_counter()
+        o = oracle.run(p, mode, steps, want_state=False)
+        dt = time.perf_counter() - t0
+        if dt > seconds_target / 3 or steps >= 64:
+            break
+        steps *= 2
+    events = float(len(o["t"])) * s["k_out"]
+    return {"value": events / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%s, first %d steps from the initial state (%d spikes), single thread"
+                      % (workload, steps, len(o["t"])),
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    cb = _cpu_baseline(args.workload)
+    cfg = W.WORKLOADS[args.workload]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": cfg["precision"],
+        "data": "synthetic", "config": {"workload": args.workload},
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _measure_net(snn, torch, cfg, seed, steps, warmup, stream):
+    """Build a net, warm it up, time `steps` graph-replayed steps."""
+    n, s = W.neuron_params(), W.synapse_params()
+    t0 = time.perf_counter()
+    net = snn.Net(cfg["grid_w"], cfg["grid_h"], n, s, seed, cfg["precision"],
+                  stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    net.step(warmup)
+    net.spikes()
+    torch.cuda.synchronize()
+    r0, e0, _ = net.stats()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    net.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    r1, e1, _ = net.stats()
+    return net, build_s, ms, r1 - r0, e1 - e0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1511_09325_gb300 import build as B
+    from paper_1511_09325_gb300 import snn
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or ws == 1:
+        B.build()
+    if ws > 1:
+        dist.barrier()
+    snn.load()
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "") or "")
+    if uuid and not uuid.startswith("GPU-"):
+        uuid = "GPU-" + uuid
+    cfg = W.WORKLOADS[args.workload]
+    stream = torch.cuda.Stream()
+    seed = cfg["seed"] + rank
+    K, Wm = args.steps, args.warmup
+
+    clocks = Clocks(uuid)
+    clocks.start()
+    net, build_s, ms, rec_ev, ext_ev = _measure_net(snn, torch, cfg, seed, K, Wm, stream)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        ev = torch.tensor([rec_ev, ext_ev], device="cuda", dtype=torch.float64)
+        dist.all_reduce(ev)
+        rec_ev, ext_ev = float(ev[0].item()), float(ev[1].item())
+    clk = clocks.stop()
+    info = net.info()
+    _, pop_hz = net.rates()
+
+    # per-kernel device time over the same kind of steps (eager launches)
+    P = min(args.profile_steps, max(K, 1))
+    kms, kbytes = net.step_profiled(P)
+    hbm, peak_kind = _peaks()
+    dom = 0 if kms[0] >= kms[1] else 1
+    kname = ["update_kernel", "deliver_kernel"][dom]
+    achieved = kbytes[dom] / (kms[dom] * 1e-3) / 1e9
+    tr = _traffic(args.workload, kname)
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+                "traffic": tr, "launches": P,
+                "kernel_ms": {"update": kms[0] / P, "deliver": kms[1] / P},
+                "kernel_gbs": {"update": kbytes[0] / (kms[0] * 1e-3) / 1e9,
+                               "deliver": kbytes[1] / (kms[1] * 1e-3) / 1e9}}
+
+    # end to end through the public API: step, then drain the step's spikes
+    # to pinned-free host arrays (device -> host copy inside the timed region)
+    net.spikes()
+    torch.cuda.synchronize()
+    E = min(args.e2e_steps, max(K, 1))
+    r0, _, _ = net.stats()
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(E):
+        net.step(1)
+        st, ids, _ = net.spikes()
+        d2h += 8 * len(st) + 40  # records plus the control block read
+    e2e_s = time.perf_counter() - t0
+    r1, _, _ = net.stats()
+    e2e = {"value": (r1 - r0) * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": d2h / E, "steps": E}
+    net.close()
+
+    extra = None
+    if not args.no_extra and ws == 1 and rank == 0:
+        extra = _precision_form(snn, torch, stream, Wm)
+
+    cpu = None
+    if rank == 0 and ws == 1:
+        cb = _cpu_baseline(args.workload)
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if ws > 1:
+        dist.barrier()
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    value = rec_ev / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+i32" if cfg["precision"] == "f32w" else "f16+i32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [cfg["grid_w"], cfg["grid_h"]],
+                   "neurons": info["neurons"], "synapses": info["synapses"],
+                   "precision": cfg["precision"], "seed": cfg["seed"],
+                   "parallelism": "replicas%d" % ws,
+                   "l2": "inputs larger than L2 (synapse table %.1f GB)" % (info["synapse_bytes"] / 1e9)},
+        "wall_s_per_model_s": (ms / K),
+        "paper_convention_events_per_s": (rec_ev + ext_ev) / (ms * 1e-3),
+        "pop_rates_hz": [float(pop_hz[0]), float(pop_hz[1])],
+        "build_s": build_s,
+        "gpu_launches": 2 * K,
+        "roofline": roofline,
+        "e2e": e2e,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    if extra:
+        line["precision_form"] = extra
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def _precision_form(snn, torch, stream, warmup, steps=1000):
+    """96x96 columns (14.17 G synapses), FP16 weights vs FP32 weights."""
+    out = {"workload": "cols96x96", "steps": steps, "warmup": warmup}
+    free, _ = torch.cuda.mem_get_info()
+    for prec in ("f16w", "f32w"):
+        cfg = W.WORKLOADS["cols96x96_" + prec]
+        need = 11427840 * (1384 * (4 if prec == "f16w" else 8) + 140)
+        if need > free * 0.97:
+            out[prec] = {"skipped": "needs %.0f GB of %.0f GB free" % (need / 1e9, free / 1e9)}
+            continue
+        net, build_s, ms, rec_ev, ext_ev = _measure_net(snn, torch, cfg, cfg["seed"], steps,
+                                                        warmup, stream)
+        _, pop = net.rates()
+        kms, kb = net.step_profiled(min(steps, 500))
+        hbm, _ = _peaks()
+        gbs = (kb[0] + kb[1]) / ((kms[0] + kms[1]) * 1e-3) / 1e9
+        out[prec] = {"events_per_s": rec_ev / (ms * 1e-3), "wall_s_per_model_s": ms / steps,
+                     "ms_per_step": ms / steps, "build_s": build_s,
+                     "pop_rates_hz": [float(pop[0]), float(pop[1])],
+                     "step_gbs": gbs, "step_frac_hbm": gbs / hbm,
+                     "deliver_gbs": kb[1] / (kms[1] * 1e-3) / 1e9,
+                     "update_gbs": kb[0] / (kms[0] * 1e-3) / 1e9}
+        net.close()
+        torch.cuda.empty_cache()
+    if "events_per_s" in out.get("f16w", {}) and "events_per_s" in out.get("f32w", {}):
+        out["fp16_speedup_wall"] = out["f32w"]["ms_per_step"] / out["f16w"]["ms_per_step"]
+    return out
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

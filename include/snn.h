@@ -1,0 +1,189 @@
+/*
+ * snn.h -- C ABI of the GB300 spiking cortical-column simulator.
+ *
+ * The model is the one measured in arxiv 1511.09325 (Sec. 2, "Methods"): a
+ * 2-D grid of cortical columns, each holding n_per_col point neurons (1240 in
+ * the paper, 80 % excitatory), leaky integrate-and-fire with spike-frequency
+ * adaptation (a calcium-driven after-hyperpolarisation current), about 1240
+ * outgoing synapses per neuron split between the own column and nearby columns
+ * with a probability decreasing with distance, plus external excitatory input,
+ * with synaptic plasticity disabled.  The simulator advances it in 1 ms steps,
+ * mixing time-driven stepping with event-driven spike delivery (Sec. 1).
+ *
+ * One step, as this library computes it:
+ *   1. every neuron i reads its input for step t (recurrent, in int32 units of
+ *      2^-16 mV, plus k_i(t) * J_ext with k_i(t) ~ Poisson(nu_ext * 1 ms) drawn
+ *      from Philox4x32-10 keyed on (seed, i, t)), integrates it, fires when
+ *      V >= theta (reset to V_reset, refractory for t_ref, calcium += dc) and
+ *      advances V and calcium by the exact 1 ms propagator of
+ *      dV/dt = -V/tau_m - g_c c, dc/dt = -c/tau_c;
+ *   2. every spike emitted in the last d_max steps delivers, through the
+ *      synapses of the matching axonal delay, its fixed-point weights into the
+ *      input of step t + 1 (integer atomics: the sum is order-independent).
+ * The fixed-point/FP32 arithmetic is bit-identical to the CPU oracle of this
+ * project; see the reading of each formula in the project's design notes.
+ *
+ * Conventions for every call:
+ *   - returns an int status (SNN_OK = 0, negative on error); no C++ exception
+ *     crosses the ABI; snn_last_error() gives a message for the last failure;
+ *   - the library owns every device allocation of a net; the caller owns the
+ *     host buffers it passes and must size them as stated;
+ *   - calls on one net are not thread-safe; different nets are independent;
+ *   - device work is enqueued on the net's stream (the caller's, if given);
+ *     snn_read_* and snn_stats synchronise that stream.
+ */
+#ifndef SNN_GB300_H
+#define SNN_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct snn_net snn_net; /* opaque, library-owned */
+
+/* Neuron model (Sec. 2: LIF with SFA; 1240 neurons per column, 80 % E).
+ * Units: ms, mV, mV/ms; rates in kHz. */
+typedef struct {
+  int32_t n_per_col; /* neurons per column, 2..2048 (1240)                */
+  int32_t n_exc;     /* excitatory neurons per column, first in the column */
+  float tau_m;       /* membrane time constant (20 ms)                     */
+  float theta;       /* firing threshold (20 mV)                           */
+  float v_reset;     /* reset potential (15 mV)                            */
+  float t_ref;       /* refractory period, rounded to whole steps (2 ms)   */
+  float tau_c;       /* calcium time constant (500 ms)                     */
+  float dc;          /* calcium increment per spike (1)                    */
+  float gc_exc;      /* adaptation gain of E neurons (0.02 mV/ms)          */
+  float gc_inh;      /* adaptation gain of I neurons (0)                   */
+  float j_ext_mV;    /* efficacy of one external event (0.4 mV)            */
+  float nu_ext_kHz;  /* external Poisson rate per neuron (2.5 kHz)         */
+} snn_neuron_params;
+
+/* Connectivity (Sec. 2: local plus distance-dependent remote synapses). */
+typedef struct {
+  int32_t k_out;          /* outgoing synapses per neuron (1240)            */
+  float frac_local;       /* fraction inside the own column (0.5)           */
+  float lambda_cols;      /* remote P ~ exp(-r / lambda), r in grid steps   */
+  int32_t stencil_radius; /* remote cut-off |dx|,|dy| <= radius, 1..3 (3)   */
+  float w_exc_mV;         /* mean weight of E synapses (0.4 mV)             */
+  float w_inh_mV;         /* mean weight of I synapses (-1.6 mV)            */
+  float w_cv;             /* coefficient of variation of weights (0.25)     */
+  int32_t d_min, d_max;   /* axonal delays, whole steps, 1 <= d_min <= d_max <= 32 */
+  int32_t periodic;       /* must be 1: the grid is a torus                  */
+} snn_synapse_params;
+
+enum {
+  SNN_OK = 0,
+  SNN_EINVAL = -1,    /* bad argument or parameter                          */
+  SNN_ENOMEM = -2,    /* device or host allocation failed                   */
+  SNN_ECUDA = -3,     /* a CUDA call failed (message in snn_last_error)     */
+  SNN_EOVERFLOW = -4, /* spike records were dropped (counters stay exact)   */
+  SNN_ETIMEOUT = -5,  /* a bounded device wait gave up                      */
+  SNN_ESTATE = -6     /* call not valid in the net's current state          */
+};
+
+/* Weight storage of the outgoing-synapse table. */
+enum {
+  SNN_EXACT_F32W = 0, /* 8 B/synapse: packed target + FP32 weight            */
+  SNN_EXACT_F16W = 1  /* 4 B/synapse: packed target + FP16 weight magnitude  */
+};
+
+/*
+ * snn_build -- construct a grid_w x grid_h network on the current device.
+ * Sec. 2: grid of columns, n_per_col neurons each, k_out outgoing synapses.
+ * seed keys every random draw (connectivity, initial V, external input).
+ * precision is SNN_EXACT_F32W or SNN_EXACT_F16W.  cuda_stream is a
+ * cudaStream_t (NULL: the library creates a non-blocking stream of its own).
+ * On success *out receives the net (destroy with snn_destroy).  Returns
+ * SNN_EINVAL for parameters outside the stated ranges, SNN_ENOMEM when the
+ * synapse table does not fit, SNN_ECUDA on a CUDA error.
+ */
+int snn_build(int grid_w, int grid_h, const snn_neuron_params* neuron,
+              const snn_synapse_params* synapse, uint64_t seed, int precision,
+              void* cuda_stream, snn_net** out);
+
+/*
+ * snn_step -- advance n_steps 1 ms steps (Sec. 1: fixed network step, spikes
+ * delivered event by event).  Asynchronous on the net's stream: the steps run
+ * as replays of a captured CUDA graph.  n_steps >= 0.
+ */
+int snn_step(snn_net* net, int64_t n_steps);
+
+/*
+ * snn_read_spikes -- drain the spike records kept since the last drain.
+ * Writes up to cap pairs (steps[k], ids[k]) in step order (order within a
+ * step unspecified) and *n_out = pairs written.  ids are global neuron
+ * indices i = (y * grid_w + x) * n_per_col + l.  Returns SNN_EOVERFLOW if the
+ * device record buffer or cap was too small; the records beyond it are lost,
+ * the counters of snn_read_rates / snn_stats are not affected.
+ */
+int snn_read_spikes(snn_net* net, int32_t* steps, int32_t* ids, int64_t cap,
+                    int64_t* n_out);
+
+/* snn_pending_spikes -- number of records a drain would return now. */
+int snn_pending_spikes(snn_net* net, int64_t* n_out);
+
+/* snn_set_record_capacity -- resize the device spike-record buffer (records,
+ * 8 B each; the default is 2^24).  Drops the pending records. */
+int snn_set_record_capacity(snn_net* net, int64_t capacity);
+
+/*
+ * snn_read_rates -- firing rates over the steps since the last call.
+ * hz[2 * c + p] = rate (Hz) of population p (0 = E, 1 = I) of column
+ * c = y * grid_w + x; n must be >= 2 * grid_w * grid_h (hz may be NULL).
+ * pop_hz[2] (may be NULL) receives the grid-wide E and I rates.
+ */
+int snn_read_rates(snn_net* net, float* hz, int64_t n, float* pop_hz);
+
+/*
+ * snn_stats -- totals since snn_build: recurrent synaptic events (spikes x
+ * k_out), external events (sum of the Poisson counts; the paper counts both,
+ * Sec. 3), and steps simulated.  Any pointer may be NULL.
+ */
+int snn_stats(snn_net* net, double* recurrent_events, double* external_events,
+              int64_t* steps);
+
+/*
+ * snn_get_state -- copy the neuron state to host arrays of N floats / bytes:
+ * membrane potential (mV), calcium, remaining refractory steps.  N = number
+ * of neurons.  Any pointer may be NULL.
+ */
+int snn_get_state(snn_net* net, float* v, float* c, uint8_t* refractory);
+
+/*
+ * snn_read_synapses -- decode the outgoing synapses of neurons j0..j0+n-1 from
+ * the device table into host arrays of n * k_out entries, grouped by neuron,
+ * within a neuron by delay: target neuron, delay (steps), weight in 2^-16 mV.
+ */
+int snn_read_synapses(snn_net* net, int64_t j0, int64_t n, int64_t* target,
+                      int32_t* delay, int32_t* wfx);
+
+/*
+ * snn_info -- sizes of the net: info[0] = N neurons, [1] = synapses,
+ * [2] = device bytes held, [3] = bytes of the synapse table, [4] = row
+ * capacity in synapse slots, [5] = precision.  n = entries available.
+ */
+int snn_info(snn_net* net, int64_t* info, int n);
+
+/*
+ * snn_step_profiled -- like snn_step, but each step's kernels are launched
+ * one by one with CUDA events around each on the net's stream.  Writes the
+ * summed device milliseconds of the neuron-update and delivery kernels and,
+ * in bytes[2], their algorithmic bytes (see the design notes) over the
+ * n_steps.  Synchronises the stream.  For measurement only.
+ */
+int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes);
+
+/* snn_last_error -- message of the last failure on net (thread-local when net
+ * is NULL).  Never NULL; valid until the next call on the same net. */
+const char* snn_last_error(const snn_net* net);
+
+/* snn_destroy -- free every resource of the net; NULL is a no-op. */
+void snn_destroy(snn_net* net);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNN_GB300_H */

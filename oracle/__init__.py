@@ -76,9 +76,10 @@ def lib():
         L.orc_neuron_trace.argtypes = [P(OrcParams), ctypes.c_int, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int64, vp, vp, vp, vp, vp]
+        L.orc_init_v.argtypes = [P(OrcParams), ctypes.c_int, ctypes.c_int64, ctypes.c_int64, vp]
         L.orc_run.argtypes = [P(OrcParams), ctypes.c_int, ctypes.c_int64,
                               ctypes.c_int64] + [vp] * 8
-        for f in ("orc_validate", "orc_tables_export", "orc_synapses",
+        for f in ("orc_validate", "orc_tables_export", "orc_synapses", "orc_init_v",
                   "orc_ext_counts", "orc_neuron_trace", "orc_run"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -166,6 +167,14 @@ def ext_counts(p, i0, n, t0, n_steps=None):
     k = np.zeros(nt * n, np.int32)
     _check(lib().orc_ext_counts(ctypes.byref(p), i0, n, t0, nt, _ptr(k)), "ext_counts")
     return k if n_steps is None else k.reshape(nt, n)
+
+
+def init_v(p, mode, i0, n):
+    """Initial membrane potentials of neurons i0..i0+n-1."""
+    mode = MODES[mode] if isinstance(mode, str) else mode
+    v = np.zeros(n, np.float64)
+    _check(lib().orc_init_v(ctypes.byref(p), mode, i0, n, _ptr(v)), "init_v")
+    return v
 
 
 def neuron_trace(p, mode, pop, v0, c0, inputs):

@@ -475,6 +475,21 @@ int orc_ext_counts(const orc_params *p, int64_t i0, int64_t n, int64_t t0,
   return ORC_OK;
 }
 
+/* Initial membrane potentials of neurons i0..i0+n-1 (as double). */
+int orc_init_v(const orc_params *p, int mode, int64_t i0, int64_t n, double *v) {
+  int64_t i;
+  int rc = validate(p);
+  if (rc) return rc;
+  for (i = 0; i < n; ++i) {
+    uint32_t u = init_word(p->seed, i0 + i);
+    if (mode == ORC_MODE_F64)
+      v[i] = (double)p->theta * ((double)(u >> 8) * 5.9604644775390625e-08);
+    else
+      v[i] = (double)(p->theta * ((float)(u >> 8) * 5.9604644775390625e-08f));
+  }
+  return ORC_OK;
+}
+
 /* Single-neuron trace driven by an explicit input sequence (no network, no
  * external Poisson input).  mode F32W/F16W: input_fx[t] in 2^-16 mV units;
  * mode F64: input_mv[t] in mV.  pop = 0 (E) or 1 (I).  Writes V, c after each

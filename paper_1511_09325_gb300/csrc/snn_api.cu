@@ -1,0 +1,591 @@
+// snn_api.cu -- the C ABI: net lifetime, graph-captured step loop, readback.
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "snn_internal.h"
+
+using namespace snn;
+
+struct snn_net {
+  // configuration
+  int W = 0, H = 0, npc = 0, nexc = 0, K = 0, dmin = 0, ndel = 0, nslot = 0;
+  int precision = 0, rowcap = 0, rec_size = 0, num_sms = 0, deliver_grid = 0;
+  long long N = 0, Npad = 0, ncol = 0;
+  uint64_t seed = 0;
+  HostTables tables;
+  StepParams sp{};
+  // device memory
+  void* syn = nullptr;
+  uint8_t* bend = nullptr;
+  float* V = nullptr;
+  float* C = nullptr;
+  uint8_t* R = nullptr;
+  int32_t* acc = nullptr;
+  uint32_t* ids = nullptr;
+  Ctl* ctl = nullptr;
+  unsigned long long* rec = nullptr;
+  long long rec_cap = 0;
+  unsigned long long* colcnt = nullptr;
+  size_t device_bytes = 0;
+  // execution
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaGraphExec_t graph_one = nullptr;
+  cudaGraphExec_t graph_many = nullptr;
+  int graph_many_steps = 64;
+  long long rate_window_start = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(snn_net* net, int code, const std::string& msg) {
+  if (net)
+    net->err = msg;
+  else
+    g_err = msg;
+  return code;
+}
+
+int cuda_fail(snn_net* net, cudaError_t e, const char* what) {
+  return fail(net, e == cudaErrorMemoryAllocation ? SNN_ENOMEM : SNN_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SNN_CUDA(net, call)                                   \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail((net), e_, #call); \
+  } while (0)
+
+template <class T>
+int dalloc(snn_net* net, T** p, size_t bytes) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, bytes ? bytes : 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(net, e == cudaErrorMemoryAllocation ? SNN_ENOMEM : SNN_ECUDA,
+                "cudaMalloc of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+  }
+  *p = static_cast<T*>(v);
+  net->device_bytes += bytes;
+  return SNN_OK;
+}
+
+void free_graphs(snn_net* net) {
+  if (net->graph_one) cudaGraphExecDestroy(net->graph_one);
+  if (net->graph_many) cudaGraphExecDestroy(net->graph_many);
+  net->graph_one = net->graph_many = nullptr;
+}
+
+void release(snn_net* net) {
+  free_graphs(net);
+  void* ptrs[] = {net->syn, net->bend, net->V, net->C, net->R, net->acc,
+                  net->ids, net->ctl, net->rec, net->colcnt};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
+}
+
+int validate(int gw, int gh, const snn_neuron_params* n, const snn_synapse_params* s,
+             int precision, std::string* why) {
+  auto bad = [&](const char* m) {
+    *why = m;
+    return SNN_EINVAL;
+  };
+  if (!n || !s) return bad("null parameter struct");
+  if (gw < 1 || gh < 1) return bad("grid must be at least 1x1");
+  if (n->n_per_col < 2 || n->n_per_col > 2048) return bad("n_per_col must be in 2..2048");
+  if (n->n_exc < 0 || n->n_exc > n->n_per_col) return bad("n_exc must be in 0..n_per_col");
+  if (!(n->tau_m > 0.f) || !(n->tau_c > 0.f)) return bad("time constants must be positive");
+  if (!(n->t_ref >= 0.f) || n->t_ref > 200.f) return bad("t_ref must be in 0..200 ms");
+  if (!(n->nu_ext_kHz >= 0.f) || n->nu_ext_kHz > 40.f) return bad("nu_ext_kHz must be in 0..40");
+  if (!std::isfinite(n->theta) || !std::isfinite(n->v_reset) || !std::isfinite(n->dc) ||
+      !std::isfinite(n->gc_exc) || !std::isfinite(n->gc_inh) || !std::isfinite(n->j_ext_mV))
+    return bad("non-finite neuron parameter");
+  if (s->k_out < 1) return bad("k_out must be positive");
+  if (!(s->frac_local >= 0.f && s->frac_local <= 1.f)) return bad("frac_local must be in [0, 1]");
+  if (!(s->lambda_cols > 0.f)) return bad("lambda_cols must be positive");
+  if (s->stencil_radius < 1 || s->stencil_radius > 3) return bad("stencil_radius must be 1..3");
+  if (s->d_min < 1 || s->d_max < s->d_min || s->d_max > kMaxDelays)
+    return bad("delays must satisfy 1 <= d_min <= d_max <= 32");
+  if (s->periodic != 1) return bad("only periodic grids are supported");
+  if (!std::isfinite(s->w_exc_mV) || !std::isfinite(s->w_inh_mV) || !std::isfinite(s->w_cv))
+    return bad("non-finite weight parameter");
+  if (precision != SNN_EXACT_F32W && precision != SNN_EXACT_F16W) return bad("unknown precision");
+  const int ndel = s->d_max - s->d_min + 1;
+  if ((s->k_out + (kSlotUnit - 1) * ndel + kSlotUnit - 1) / kSlotUnit > 255)
+    return bad("k_out too large for 8-bit bucket ends");
+  const long long N = (long long)gw * gh * n->n_per_col;
+  if (N >= (1LL << 31) - 4) return bad("too many neurons");
+  return SNN_OK;
+}
+
+int capture(snn_net* net, int steps, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  SNN_CUDA(net, cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  for (int s = 0; s < steps && le == cudaSuccess; ++s) {
+    le = launch_update(net->sp, net->stream);
+    if (le == cudaSuccess) le = launch_deliver(net->sp, net->precision, net->deliver_grid, net->stream);
+  }
+  cudaError_t ee = cudaStreamEndCapture(net->stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(net, le, "kernel launch during capture");
+  }
+  if (ee != cudaSuccess) return cuda_fail(net, ee, "cudaStreamEndCapture");
+  cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return cuda_fail(net, ie, "cudaGraphInstantiate");
+  return SNN_OK;
+}
+
+void fill_step_params(snn_net* net) {
+  StepParams& p = net->sp;
+  const HostTables& t = net->tables;
+  p.N = net->N;
+  p.npc = net->npc;
+  p.nexc = net->nexc;
+  p.W = net->W;
+  p.H = net->H;
+  p.K = net->K;
+  p.dmin = net->dmin;
+  p.ndel = net->ndel;
+  p.nslot = net->nslot;
+  p.rowcap = net->rowcap;
+  p.seed_lo = (uint32_t)(net->seed & 0xFFFFFFFFu);
+  p.seed_hi = (uint32_t)(net->seed >> 32);
+  p.pvv = t.pvv;
+  p.pcc = t.pcc;
+  p.pvc_e = t.pvc[0];
+  p.pvc_i = t.pvc[1];
+  p.jx = t.jx;
+  p.nref = t.nref;
+  p.n_pois_thr = t.n_pois_thr;
+  std::memcpy(p.pois_thr, t.pois_thr, sizeof(p.pois_thr));
+  std::memcpy(p.pois_guide, t.pois_guide, sizeof(p.pois_guide));
+  p.V = net->V;
+  p.C = net->C;
+  p.R = net->R;
+  p.acc = net->acc;
+  p.ids = net->ids;
+  p.bend = net->bend;
+  p.syn = net->syn;
+  p.ctl = net->ctl;
+  p.rec = net->rec;
+  p.rec_cap = net->rec_cap;
+  p.colcnt = net->colcnt;
+}
+
+int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
+               const snn_synapse_params* sp, uint64_t seed, int precision) {
+  std::string why;
+  int rc = validate(gw, gh, np, sp, precision, &why);
+  if (rc != SNN_OK) return fail(net, rc, why);
+  net->W = gw;
+  net->H = gh;
+  net->npc = np->n_per_col;
+  net->nexc = np->n_exc;
+  net->K = sp->k_out;
+  net->dmin = sp->d_min;
+  net->ndel = sp->d_max - sp->d_min + 1;
+  net->nslot = sp->d_max;
+  net->precision = precision;
+  net->seed = seed;
+  net->ncol = (long long)gw * gh;
+  net->N = net->ncol * np->n_per_col;
+  net->Npad = (net->N + 3) / 4 * 4;
+  net->rec_size = precision == SNN_EXACT_F16W ? 4 : 8;
+  net->rowcap = (sp->k_out + (kSlotUnit - 1) * net->ndel + kSlotUnit - 1) / kSlotUnit * kSlotUnit;
+  net->rec_cap = 1LL << 24;
+  rc = make_host_tables(*np, *sp, precision, &net->tables, &why);
+  if (rc != SNN_OK) return fail(net, rc, why);
+  net->sp.theta = np->theta;
+  net->sp.vr = np->v_reset;
+  net->sp.dc = np->dc;
+
+  int dev = 0;
+  SNN_CUDA(net, cudaGetDevice(&dev));
+  SNN_CUDA(net, cudaDeviceGetAttribute(&net->num_sms, cudaDevAttrMultiProcessorCount, dev));
+
+  const size_t syn_bytes = (size_t)net->N * net->rowcap * net->rec_size;
+  if ((rc = dalloc(net, &net->syn, syn_bytes))) return rc;
+  if ((rc = dalloc(net, &net->bend, (size_t)net->N * kBendStride))) return rc;
+  if ((rc = dalloc(net, &net->V, (size_t)net->Npad * 4))) return rc;
+  if ((rc = dalloc(net, &net->C, (size_t)net->Npad * 4))) return rc;
+  if ((rc = dalloc(net, &net->R, (size_t)net->Npad))) return rc;
+  if ((rc = dalloc(net, &net->acc, (size_t)net->Npad * 4))) return rc;
+  if ((rc = dalloc(net, &net->ids, (size_t)net->nslot * net->N * 4))) return rc;
+  if ((rc = dalloc(net, &net->ctl, sizeof(Ctl)))) return rc;
+  if ((rc = dalloc(net, &net->rec, (size_t)net->rec_cap * 8))) return rc;
+  if ((rc = dalloc(net, &net->colcnt, (size_t)net->ncol * 2 * 8))) return rc;
+  uint32_t* wtab = nullptr;
+  if ((rc = dalloc(net, &wtab, net->tables.wtab.size() * 4))) return rc;
+  net->device_bytes -= net->tables.wtab.size() * 4;
+
+  cudaError_t e = cudaMemcpyAsync(wtab, net->tables.wtab.data(), net->tables.wtab.size() * 4,
+                                  cudaMemcpyHostToDevice, net->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(net->ctl, 0, sizeof(Ctl), net->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(net->colcnt, 0, (size_t)net->ncol * 16, net->stream);
+  if (e == cudaSuccess) {
+    BuildParams bp{};
+    bp.N = net->N;
+    bp.npc = net->npc;
+    bp.nexc = net->nexc;
+    bp.W = net->W;
+    bp.H = net->H;
+    bp.K = net->K;
+    bp.k_local = net->tables.k_local;
+    bp.dmin = net->dmin;
+    bp.ndel = net->ndel;
+    bp.rowcap = net->rowcap;
+    bp.n_off = net->tables.n_off;
+    bp.seed_lo = (uint32_t)(seed & 0xFFFFFFFFu);
+    bp.seed_hi = (uint32_t)(seed >> 32);
+    std::memcpy(bp.stencil_thr, net->tables.stencil_thr, sizeof(bp.stencil_thr));
+    std::memcpy(bp.off_dx, net->tables.off_dx, sizeof(bp.off_dx));
+    std::memcpy(bp.off_dy, net->tables.off_dy, sizeof(bp.off_dy));
+    bp.wtab = wtab;
+    bp.syn = net->syn;
+    bp.bend = net->bend;
+    e = launch_build(bp, precision, net->num_sms, net->stream);
+  }
+  fill_step_params(net);
+  if (e == cudaSuccess) e = launch_init_state(net->sp, net->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+  cudaFree(wtab);
+  if (e != cudaSuccess) return cuda_fail(net, e, "network construction");
+  net->deliver_grid = deliver_grid(precision, net->num_sms);
+  return SNN_OK;
+}
+
+int sync(snn_net* net) {
+  SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+  return SNN_OK;
+}
+
+Ctl read_ctl(snn_net* net, cudaError_t* e) {
+  Ctl c{};
+  *e = cudaMemcpyAsync(&c, net->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, net->stream);
+  if (*e == cudaSuccess) *e = cudaStreamSynchronize(net->stream);
+  return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+int snn_build(int grid_w, int grid_h, const snn_neuron_params* neuron,
+              const snn_synapse_params* synapse, uint64_t seed, int precision,
+              void* cuda_stream, snn_net** out) {
+  if (!out) return fail(nullptr, SNN_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  const int vrc = validate(grid_w, grid_h, neuron, synapse, precision, &why);
+  if (vrc != SNN_OK) return fail(nullptr, vrc, why);
+  snn_net* net = new (std::nothrow) snn_net();
+  if (!net) return fail(nullptr, SNN_ENOMEM, "host allocation failed");
+  if (cuda_stream) {
+    net->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete net;
+      return fail(nullptr, SNN_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    net->own_stream = true;
+  }
+  int rc = build_impl(net, grid_w, grid_h, neuron, synapse, seed, precision);
+  if (rc != SNN_OK) {
+    g_err = net->err;
+    release(net);
+    delete net;
+    return rc;
+  }
+  *out = net;
+  return SNN_OK;
+}
+
+int snn_step(snn_net* net, int64_t n_steps) {
+  if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
+  if (n_steps < 0) return fail(net, SNN_EINVAL, "n_steps must be >= 0");
+  if (n_steps == 0) return SNN_OK;
+  int rc;
+  if (n_steps >= net->graph_many_steps && !net->graph_many)
+    if ((rc = capture(net, net->graph_many_steps, &net->graph_many))) return rc;
+  if (!net->graph_one)
+    if ((rc = capture(net, 1, &net->graph_one))) return rc;
+  int64_t left = n_steps;
+  while (left >= net->graph_many_steps) {
+    SNN_CUDA(net, cudaGraphLaunch(net->graph_many, net->stream));
+    left -= net->graph_many_steps;
+  }
+  while (left-- > 0) SNN_CUDA(net, cudaGraphLaunch(net->graph_one, net->stream));
+  return SNN_OK;
+}
+
+int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes) {
+  if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
+  if (n_steps < 0) return fail(net, SNN_EINVAL, "n_steps must be >= 0");
+  std::vector<cudaEvent_t> ev((size_t)n_steps * 3 + 1);
+  std::vector<unsigned long long> spikes((size_t)n_steps + 1, 0ull);
+  unsigned long long* hspk = nullptr;
+  SNN_CUDA(net, cudaMallocHost(&hspk, ((size_t)n_steps + 1) * 8));
+  int rc = SNN_OK;
+  size_t made = 0;
+  cudaError_t e = cudaSuccess;
+  for (; made < ev.size() && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+  if (e != cudaSuccess) --made;
+  const size_t off_spk = offsetof(Ctl, spikes);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hspk, (char*)net->ctl + off_spk, 8, cudaMemcpyDeviceToHost, net->stream);
+  for (int64_t s = 0; s < n_steps && e == cudaSuccess; ++s) {
+    e = cudaEventRecord(ev[3 * s], net->stream);
+    if (e == cudaSuccess) e = launch_update(net->sp, net->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], net->stream);
+    if (e == cudaSuccess) e = launch_deliver(net->sp, net->precision, net->deliver_grid, net->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], net->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hspk + s + 1, (char*)net->ctl + off_spk, 8, cudaMemcpyDeviceToHost,
+                          net->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+  double t_up = 0.0, t_dl = 0.0, b_up = 0.0, b_dl = 0.0;
+  if (e == cudaSuccess) {
+    const double neuron_bytes = 26.0 * (double)net->N;
+    for (int64_t s = 0; s < n_steps; ++s) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
+      cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]);
+      t_up += a;
+      t_dl += b;
+      const double S = (double)(hspk[s + 1] - hspk[s]);
+      b_up += neuron_bytes + 12.0 * S;
+      b_dl += S * ((double)net->K * net->rec_size + 6.0 * net->ndel);
+    }
+  } else {
+    rc = cuda_fail(net, e, "profiled step");
+  }
+  for (size_t i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+  cudaFreeHost(hspk);
+  if (rc == SNN_OK) {
+    if (ms) {
+      ms[0] = t_up;
+      ms[1] = t_dl;
+    }
+    if (bytes) {
+      bytes[0] = b_up;
+      bytes[1] = b_dl;
+    }
+  }
+  return rc;
+}
+
+int snn_pending_spikes(snn_net* net, int64_t* n_out) {
+  if (!net || !n_out) return fail(net, SNN_EINVAL, "null argument");
+  cudaError_t e;
+  Ctl c = read_ctl(net, &e);
+  if (e != cudaSuccess) return cuda_fail(net, e, "read control block");
+  *n_out = (int64_t)(c.rec_count < (unsigned long long)net->rec_cap ? c.rec_count : net->rec_cap);
+  return SNN_OK;
+}
+
+int snn_read_spikes(snn_net* net, int32_t* steps, int32_t* ids, int64_t cap, int64_t* n_out) {
+  if (!net || !n_out || cap < 0 || (cap > 0 && (!steps || !ids)))
+    return fail(net, SNN_EINVAL, "bad argument");
+  *n_out = 0;
+  cudaError_t e;
+  Ctl c = read_ctl(net, &e);
+  if (e != cudaSuccess) return cuda_fail(net, e, "read control block");
+  const long long kept = (long long)(c.rec_count < (unsigned long long)net->rec_cap ? c.rec_count
+                                                                                  : net->rec_cap);
+  const long long n = kept < cap ? kept : cap;
+  bool lost = c.rec_overflow != 0u || kept > cap;
+  if (n > 0) {
+    std::vector<unsigned long long> h((size_t)n);
+    SNN_CUDA(net, cudaMemcpyAsync(h.data(), net->rec, (size_t)n * 8, cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+    // records of one step are contiguous and steps appear in order
+    for (long long k = 0; k < n; ++k) {
+      steps[k] = (int32_t)(h[k] >> 32);
+      ids[k] = (int32_t)(h[k] & 0xFFFFFFFFull);
+    }
+  }
+  const unsigned long long zero = 0ull;
+  const unsigned zero32 = 0u;
+  SNN_CUDA(net, cudaMemcpyAsync((char*)net->ctl + offsetof(Ctl, rec_count), &zero, 8,
+                                cudaMemcpyHostToDevice, net->stream));
+  SNN_CUDA(net, cudaMemcpyAsync((char*)net->ctl + offsetof(Ctl, rec_overflow), &zero32, 4,
+                                cudaMemcpyHostToDevice, net->stream));
+  SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+  *n_out = n;
+  if (lost) return fail(net, SNN_EOVERFLOW, "spike records dropped (buffer or cap too small)");
+  return SNN_OK;
+}
+
+int snn_set_record_capacity(snn_net* net, int64_t capacity) {
+  if (!net || capacity < 1) return fail(net, SNN_EINVAL, "bad argument");
+  int rc = sync(net);
+  if (rc) return rc;
+  unsigned long long* nr = nullptr;
+  cudaError_t e = cudaMalloc(&nr, (size_t)capacity * 8);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(net, e, "cudaMalloc record buffer");
+  }
+  cudaFree(net->rec);
+  net->device_bytes += ((size_t)capacity - (size_t)net->rec_cap) * 8;
+  net->rec = nr;
+  net->rec_cap = capacity;
+  fill_step_params(net);
+  free_graphs(net);
+  const unsigned long long zero = 0ull;
+  const unsigned zero32 = 0u;
+  SNN_CUDA(net, cudaMemcpyAsync((char*)net->ctl + offsetof(Ctl, rec_count), &zero, 8,
+                                cudaMemcpyHostToDevice, net->stream));
+  SNN_CUDA(net, cudaMemcpyAsync((char*)net->ctl + offsetof(Ctl, rec_overflow), &zero32, 4,
+                                cudaMemcpyHostToDevice, net->stream));
+  return sync(net);
+}
+
+int snn_read_rates(snn_net* net, float* hz, int64_t n, float* pop_hz) {
+  if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
+  if (hz && n < 2 * net->ncol) return fail(net, SNN_EINVAL, "hz array too small");
+  cudaError_t e;
+  Ctl c = read_ctl(net, &e);
+  if (e != cudaSuccess) return cuda_fail(net, e, "read control block");
+  std::vector<unsigned long long> cnt((size_t)net->ncol * 2);
+  SNN_CUDA(net, cudaMemcpyAsync(cnt.data(), net->colcnt, cnt.size() * 8, cudaMemcpyDeviceToHost,
+                                net->stream));
+  SNN_CUDA(net, cudaMemsetAsync(net->colcnt, 0, cnt.size() * 8, net->stream));
+  SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+  const long long window = c.t - net->rate_window_start;
+  net->rate_window_start = c.t;
+  const double secs = (double)window * 1e-3;
+  const double nE = (double)net->nexc, nI = (double)(net->npc - net->nexc);
+  double totE = 0.0, totI = 0.0;
+  for (long long k = 0; k < net->ncol; ++k) {
+    totE += (double)cnt[2 * k];
+    totI += (double)cnt[2 * k + 1];
+    if (hz) {
+      hz[2 * k] = (secs > 0 && nE > 0) ? (float)((double)cnt[2 * k] / (nE * secs)) : 0.f;
+      hz[2 * k + 1] = (secs > 0 && nI > 0) ? (float)((double)cnt[2 * k + 1] / (nI * secs)) : 0.f;
+    }
+  }
+  if (pop_hz) {
+    pop_hz[0] = (secs > 0 && nE > 0) ? (float)(totE / (nE * net->ncol * secs)) : 0.f;
+    pop_hz[1] = (secs > 0 && nI > 0) ? (float)(totI / (nI * net->ncol * secs)) : 0.f;
+  }
+  return SNN_OK;
+}
+
+int snn_stats(snn_net* net, double* recurrent_events, double* external_events, int64_t* steps) {
+  if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
+  cudaError_t e;
+  Ctl c = read_ctl(net, &e);
+  if (e != cudaSuccess) return cuda_fail(net, e, "read control block");
+  if (recurrent_events) *recurrent_events = (double)c.spikes * (double)net->K;
+  if (external_events) *external_events = (double)c.ext_events;
+  if (steps) *steps = (int64_t)c.t;
+  return SNN_OK;
+}
+
+int snn_get_state(snn_net* net, float* v, float* c, uint8_t* refractory) {
+  if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
+  const size_t N = (size_t)net->N;
+  if (v) SNN_CUDA(net, cudaMemcpyAsync(v, net->V, N * 4, cudaMemcpyDeviceToHost, net->stream));
+  if (c) SNN_CUDA(net, cudaMemcpyAsync(c, net->C, N * 4, cudaMemcpyDeviceToHost, net->stream));
+  if (refractory)
+    SNN_CUDA(net, cudaMemcpyAsync(refractory, net->R, N, cudaMemcpyDeviceToHost, net->stream));
+  return sync(net);
+}
+
+int snn_read_synapses(snn_net* net, int64_t j0, int64_t n, int64_t* target, int32_t* delay,
+                      int32_t* wfx) {
+  if (!net || j0 < 0 || n < 0 || j0 + n > net->N || (n > 0 && (!target || !delay || !wfx)))
+    return fail(net, SNN_EINVAL, "bad argument");
+  if (n == 0) return SNN_OK;
+  const size_t row_bytes = (size_t)net->rowcap * net->rec_size;
+  std::vector<uint8_t> rows((size_t)n * row_bytes);
+  std::vector<uint8_t> ends((size_t)n * kBendStride);
+  SNN_CUDA(net, cudaMemcpyAsync(rows.data(), (const char*)net->syn + (size_t)j0 * row_bytes,
+                                rows.size(), cudaMemcpyDeviceToHost, net->stream));
+  SNN_CUDA(net, cudaMemcpyAsync(ends.data(), net->bend + (size_t)j0 * kBendStride, ends.size(),
+                                cudaMemcpyDeviceToHost, net->stream));
+  int rc = sync(net);
+  if (rc) return rc;
+  long long o = 0;
+  for (int64_t r = 0; r < n; ++r) {
+    const long long j = j0 + r;
+    const long long col = j / net->npc;
+    const int cy = (int)(col / net->W), cx = (int)(col % net->W);
+    const bool exc = (int)(j % net->npc) < net->nexc;
+    int beg = 0;
+    for (int b = 0; b < net->ndel; ++b) {
+      const int end = ends[(size_t)r * kBendStride + b] * kSlotUnit;
+      for (int s = beg; s < end; ++s) {
+        uint32_t code, wbits;
+        const uint8_t* rp = rows.data() + (size_t)r * row_bytes + (size_t)s * net->rec_size;
+        int32_t w;
+        if (net->precision == SNN_EXACT_F16W) {
+          uint32_t rec;
+          std::memcpy(&rec, rp, 4);
+          if (rec == kPad) continue;
+          code = rec & 0x1FFFFu;
+          __half_raw hr;
+          hr.x = (unsigned short)(rec >> 17);
+          const float f = __half2float(__half(hr));
+          w = (int32_t)std::rint((exc ? f : -f) * 65536.0f);
+        } else {
+          std::memcpy(&code, rp, 4);
+          std::memcpy(&wbits, rp + 4, 4);
+          if (code == kPad) continue;
+          float f;
+          std::memcpy(&f, &wbits, 4);
+          w = (int32_t)std::rint(f * 65536.0f);
+        }
+        if (o >= (long long)n * net->K) return fail(net, SNN_ESTATE, "row holds too many synapses");
+        const int dy = (int)((code >> 14) & 7u) - 3, dx = (int)((code >> 11) & 7u) - 3;
+        const int ty = ((cy + dy) % net->H + net->H) % net->H;
+        const int tx = ((cx + dx) % net->W + net->W) % net->W;
+        target[o] = ((long long)ty * net->W + tx) * net->npc + (code & 0x7FFu);
+        delay[o] = net->dmin + b;
+        wfx[o] = w;
+        ++o;
+      }
+      beg = end;
+    }
+  }
+  if (o != (long long)n * net->K) return fail(net, SNN_ESTATE, "row holds too few synapses");
+  return SNN_OK;
+}
+
+int snn_info(snn_net* net, int64_t* info, int n) {
+  if (!net || !info) return fail(net, SNN_EINVAL, "null argument");
+  const int64_t v[6] = {net->N, net->N * (int64_t)net->K, (int64_t)net->device_bytes,
+                        net->N * (int64_t)net->rowcap * net->rec_size, net->rowcap,
+                        net->precision};
+  for (int i = 0; i < n && i < 6; ++i) info[i] = v[i];
+  return SNN_OK;
+}
+
+const char* snn_last_error(const snn_net* net) {
+  return net ? net->err.c_str() : g_err.c_str();
+}
+
+void snn_destroy(snn_net* net) {
+  if (!net) return;
+  if (net->stream) cudaStreamSynchronize(net->stream);
+  release(net);
+  delete net;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// snn_build.cu -- on-device construction of the delay-bucketed synapse table.
+//
+// Connectivity of arxiv 1511.09325, Sec. 2, as read by this library: synapse
+// k of neuron j (column (x, y), index l_j in it) draws one Philox4x32-10 block
+// (counter (j, k, CONN, 0)) = (x0, x1, x2, x3):
+//   k <  k_local : target in the own column, l = u_{n-1}(x0), skipping l_j;
+//   k >= k_local : stencil offset = first m with x1 < thr[m] (P ~ exp(-r/lambda)),
+//                  target l = u_n(x0) in column ((x+dx) mod W, (y+dy) mod H);
+//   delay d = d_min + u_ndel(x2);  weight = table[population][x3 >> 16].
+// One warp owns one row: a first pass counts the synapses of every delay
+// bucket, a second pass regenerates them and stores each into its bucket in
+// k order (warp match + popc rank), then the bucket tails are padded.
+#include "snn_device.cuh"
+#include "snn_internal.h"
+
+namespace snn {
+namespace {
+
+constexpr int kBuildWarps = 8;
+
+template <int PREC>
+__global__ void __launch_bounds__(kBuildWarps * 32)
+    build_rows_kernel(const BuildParams P) {
+  __shared__ unsigned s_cnt[kBuildWarps][32];
+  __shared__ unsigned s_cur[kBuildWarps][32];
+  __shared__ uint32_t s_thr[kMaxOff];
+  __shared__ int s_code[kMaxOff];
+  for (int m = threadIdx.x; m < kMaxOff; m += blockDim.x) {
+    s_thr[m] = P.stencil_thr[m];
+    s_code[m] = m < P.n_off ? ((P.off_dy[m] + 3) << 3) | (P.off_dx[m] + 3) : kCenterCode;
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * kBuildWarps;
+  const uint32_t ndel = (uint32_t)P.ndel;
+
+  for (long long j = (long long)blockIdx.x * kBuildWarps + w; j < P.N; j += nwarps) {
+    const uint32_t jj = (uint32_t)j;
+    s_cnt[w][lane] = 0u;
+    __syncwarp();
+    // pass 1: synapses per delay bucket
+    for (int k = lane; k < P.K; k += 32) {
+      const uint4 x = philox4x32_10(make_uint4(jj, (uint32_t)k, kTagConn, 0u), P.seed_lo, P.seed_hi);
+      atomicAdd(&s_cnt[w][below(x.z, ndel)], 1u);
+    }
+    __syncwarp();
+    const unsigned units = lane < P.ndel ? (s_cnt[w][lane] + (kSlotUnit - 1)) / kSlotUnit : 0u;
+    unsigned incl = units;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    P.bend[j * kBendStride + lane] = (uint8_t)(lane < P.ndel ? incl : 0u);
+    s_cur[w][lane] = (incl - units) * kSlotUnit;
+    __syncwarp();
+
+    const long long row = j * (long long)P.rowcap;
+    const int col = (int)(j / P.npc);
+    const int lj = (int)(j - (long long)col * P.npc);
+    const uint32_t* wt = P.wtab + (lj < P.nexc ? 0 : 65536);
+    // pass 2: regenerate and place every synapse
+    for (int k0 = 0; k0 < P.K; k0 += 32) {
+      const int k = k0 + lane;
+      const bool valid = k < P.K;
+      const uint4 x = philox4x32_10(make_uint4(jj, (uint32_t)k, kTagConn, 0u), P.seed_lo, P.seed_hi);
+      const int b = valid ? (int)below(x.z, ndel) : 63;
+      uint32_t code;
+      if (k < P.k_local) {
+        uint32_t l = below(x.x, (uint32_t)(P.npc - 1));
+        l += (l >= (uint32_t)lj) ? 1u : 0u;
+        code = ((uint32_t)kCenterCode << 11) | l;
+      } else {
+        int m = 0;
+        for (int i = 0; i + 1 < P.n_off; ++i) m += (x.y >= s_thr[i]) ? 1 : 0;
+        code = ((uint32_t)s_code[m] << 11) | below(x.x, (uint32_t)P.npc);
+      }
+      const uint32_t wbits = wt[x.w >> 16];
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, b);
+      const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+      const unsigned pos = s_cur[w][b & 31] + rank;
+      __syncwarp();
+      if (valid) {
+        if (PREC == SNN_EXACT_F16W)
+          static_cast<uint32_t*>(P.syn)[row + pos] = ((wbits & 0x7FFFu) << 17) | code;
+        else
+          static_cast<uint2*>(P.syn)[row + pos] = make_uint2(code, wbits);
+        if (rank == 0) s_cur[w][b] += __popc(peers);
+      }
+      __syncwarp();
+    }
+    // pad every bucket up to its 8-slot boundary
+    if (lane < P.ndel) {
+      const unsigned end = incl * kSlotUnit;
+      for (unsigned s = s_cur[w][lane]; s < end; ++s) {
+        if (PREC == SNN_EXACT_F16W)
+          static_cast<uint32_t*>(P.syn)[row + s] = kPad;
+        else
+          static_cast<uint2*>(P.syn)[row + s] = make_uint2(kPad, 0u);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Initial state: V_i uniform in [0, theta) at 24-bit resolution from word
+// i mod 4 of Philox(i / 4, 0, INIT); calcium, refractoriness and input zero.
+__global__ void __launch_bounds__(256) init_state_kernel(const StepParams P) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long i0 = q * 4;
+  if (i0 >= P.N) return;
+  const uint4 u = philox4x32_10(make_uint4((uint32_t)q, 0u, kTagInit, 0u), P.seed_lo, P.seed_hi);
+  const float s = 5.9604644775390625e-08f;  // 2^-24
+  float4 v;
+  v.x = __fmul_rn(P.theta, __fmul_rn(__uint2float_rn(u.x >> 8), s));
+  v.y = __fmul_rn(P.theta, __fmul_rn(__uint2float_rn(u.y >> 8), s));
+  v.z = __fmul_rn(P.theta, __fmul_rn(__uint2float_rn(u.z >> 8), s));
+  v.w = __fmul_rn(P.theta, __fmul_rn(__uint2float_rn(u.w >> 8), s));
+  reinterpret_cast<float4*>(P.V)[q] = v;
+  reinterpret_cast<float4*>(P.C)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  reinterpret_cast<int4*>(P.acc)[q] = make_int4(0, 0, 0, 0);
+  reinterpret_cast<uchar4*>(P.R)[q] = make_uchar4(0, 0, 0, 0);
+}
+
+}  // namespace
+
+cudaError_t launch_build(const BuildParams& bp, int precision, int num_sms,
+                         cudaStream_t st) {
+  const int grid = num_sms * 8;
+  if (precision == SNN_EXACT_F16W)
+    build_rows_kernel<SNN_EXACT_F16W><<<grid, kBuildWarps * 32, 0, st>>>(bp);
+  else
+    build_rows_kernel<SNN_EXACT_F32W><<<grid, kBuildWarps * 32, 0, st>>>(bp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(const StepParams& p, cudaStream_t st) {
+  const long long quads = (p.N + 3) / 4;
+  const unsigned grid = (unsigned)((quads + 255) / 256);
+  init_state_kernel<<<grid, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace snn

@@ -1,0 +1,119 @@
+// snn_internal.h -- types shared by the translation units of the library.
+//
+// Device data layout of one net (all arrays are library-owned, 256 B aligned):
+//   syn    outgoing-synapse table, row j at j * rowcap slots.  A row holds the
+//          neuron's k_out synapses grouped by delay bucket b = d - d_min; every
+//          bucket starts on a multiple of 8 slots and is padded with PAD
+//          records up to the next multiple of 8 (so a bucket is a whole number
+//          of 32 B sectors in the F16W layout).
+//            F16W: u32 record  = half_magnitude(15) << 17 | code(17)
+//            F32W: u32x2 record = { code(17), float weight bits }
+//          code = ((dy + 3) << 3 | (dx + 3)) << 11 | l  (stencil offset of the
+//          target column and index l inside it; local synapses use dx=dy=0).
+//          The weight's sign is the source population's (Dale's principle),
+//          so the F16W record drops the half's sign bit without loss.
+//   bend   u8[N][32]: bend[j][b] = end of bucket b of row j in units of 8 slots.
+//   V, C   float[Npad] membrane potential (mV) and calcium.
+//   R      u8[Npad] remaining refractory steps.
+//   acc    int32[Npad] recurrent input of the next step, 2^-16 mV units.
+//   ids    u32[d_max][N] spike lists of the last d_max steps (slot t % d_max).
+//   ctl    control block (step counter, per-slot spike counts, totals).
+//   rec    u64 spike records (step << 32 | id), drained by snn_read_spikes.
+//   colcnt u64[ncol][2] spike counts per column and population.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "snn.h"
+
+namespace snn {
+
+constexpr uint32_t kTagConn = 1u;  // Philox counter word 2 of each stream
+constexpr uint32_t kTagExt = 2u;
+constexpr uint32_t kTagInit = 3u;
+constexpr int kMaxDelays = 32;   // d_max <= 32
+constexpr int kBendStride = 32;  // bytes of bucket ends per neuron
+constexpr int kSlotUnit = 8;     // buckets are padded to 8 synapse slots
+constexpr int kMaxPoisThr = 127; // Poisson thresholds below 2^32
+constexpr int kMaxOff = 48;      // remote stencil offsets (radius <= 3)
+constexpr uint32_t kPad = 0xFFFFFFFFu;  // code of a padding record
+constexpr int kCenterCode = (3 << 3) | 3;
+
+// Tables computed on the host in FP64 and rounded once.
+struct HostTables {
+  int n_off = 0;
+  int8_t off_dx[kMaxOff] = {}, off_dy[kMaxOff] = {};
+  uint32_t stencil_thr[kMaxOff] = {};  // first n_off - 1 used; last is 2^32
+  int n_pois_thr = 0;                  // thresholds below 2^32
+  uint32_t pois_thr[kMaxPoisThr + 1] = {};
+  uint8_t pois_guide[256] = {};        // #thresholds <= (b << 24)
+  std::vector<uint32_t> wtab;          // [2][65536] stored weight bits
+  float pvv = 0, pcc = 0, pvc[2] = {0, 0};
+  int32_t jx = 0;
+  int nref = 0;
+  int k_local = 0;
+};
+
+int make_host_tables(const snn_neuron_params& np, const snn_synapse_params& sp,
+                     int precision, HostTables* out, std::string* err);
+
+// Device control block.
+struct Ctl {
+  long long t;                          // step index of the next update
+  unsigned int count[kMaxDelays];       // spikes emitted by the step in slot s
+  unsigned long long rec_count;         // records appended since the last drain
+  unsigned int rec_overflow;            // set when a record did not fit
+  unsigned int done;                    // delivery blocks finished this step
+  unsigned long long ext_events;        // sum of external Poisson counts
+  unsigned long long spikes;            // spikes since build
+};
+
+// Everything a step kernel needs, passed by value (constant bank).
+struct StepParams {
+  long long N;
+  int npc, nexc, W, H, K, dmin, ndel, nslot, rowcap;
+  uint32_t seed_lo, seed_hi;
+  float theta, vr, dc, pvv, pcc, pvc_e, pvc_i;
+  int32_t jx;
+  int nref;
+  int n_pois_thr;
+  uint32_t pois_thr[kMaxPoisThr + 1];
+  uint8_t pois_guide[256];
+  float* V;
+  float* C;
+  uint8_t* R;
+  int32_t* acc;
+  uint32_t* ids;
+  const uint8_t* bend;
+  const void* syn;
+  Ctl* ctl;
+  unsigned long long* rec;
+  long long rec_cap;
+  unsigned long long* colcnt;
+};
+
+struct BuildParams {
+  long long N;
+  int npc, nexc, W, H, K, k_local, dmin, ndel, rowcap, n_off;
+  uint32_t seed_lo, seed_hi;
+  uint32_t stencil_thr[kMaxOff];
+  int8_t off_dx[kMaxOff], off_dy[kMaxOff];
+  const uint32_t* wtab;
+  void* syn;
+  uint8_t* bend;
+};
+
+// Kernel launchers (snn_build.cu / snn_step.cu).
+cudaError_t launch_build(const BuildParams& bp, int precision, int num_sms,
+                         cudaStream_t st);
+cudaError_t launch_init_state(const StepParams& p, cudaStream_t st);
+cudaError_t launch_update(const StepParams& p, cudaStream_t st);
+cudaError_t launch_deliver(const StepParams& p, int precision, int grid,
+                           cudaStream_t st);
+int deliver_grid(int precision, int num_sms);
+
+}  // namespace snn

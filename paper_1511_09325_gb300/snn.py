@@ -1,0 +1,251 @@
+"""ctypes binding of the C ABI declared in ``include/snn.h``.
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library ``libsnn_gb300.so``.  There is no CPU fallback -- if the library is
+missing or no GPU is present the calls raise.  Function names follow the C
+ABI (``snn_build``, ``snn_step``, ...); :class:`Net` wraps them for Python.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsnn_gb300.so")
+
+SNN_OK, SNN_EINVAL, SNN_ENOMEM, SNN_ECUDA, SNN_EOVERFLOW, SNN_ETIMEOUT, SNN_ESTATE = (
+    0, -1, -2, -3, -4, -5, -6)
+SNN_EXACT_F32W, SNN_EXACT_F16W = 0, 1
+PRECISIONS = {"f32w": SNN_EXACT_F32W, "f16w": SNN_EXACT_F16W}
+
+# every symbol the header declares
+EXPORTS = ("snn_build", "snn_step", "snn_read_spikes", "snn_pending_spikes",
+           "snn_set_record_capacity", "snn_read_rates", "snn_stats", "snn_get_state",
+           "snn_read_synapses", "snn_info", "snn_step_profiled", "snn_last_error",
+           "snn_destroy")
+
+
+class SnnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("snn error %d: %s" % (code, msg))
+        self.code = code
+
+
+class NeuronParams(ctypes.Structure):
+    _fields_ = [("n_per_col", ctypes.c_int32), ("n_exc", ctypes.c_int32),
+                ("tau_m", ctypes.c_float), ("theta", ctypes.c_float),
+                ("v_reset", ctypes.c_float), ("t_ref", ctypes.c_float),
+                ("tau_c", ctypes.c_float), ("dc", ctypes.c_float),
+                ("gc_exc", ctypes.c_float), ("gc_inh", ctypes.c_float),
+                ("j_ext_mV", ctypes.c_float), ("nu_ext_kHz", ctypes.c_float)]
+
+
+class SynapseParams(ctypes.Structure):
+    _fields_ = [("k_out", ctypes.c_int32), ("frac_local", ctypes.c_float),
+                ("lambda_cols", ctypes.c_float), ("stencil_radius", ctypes.c_int32),
+                ("w_exc_mV", ctypes.c_float), ("w_inh_mV", ctypes.c_float),
+                ("w_cv", ctypes.c_float), ("d_min", ctypes.c_int32),
+                ("d_max", ctypes.c_int32), ("periodic", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("CUDA library %s not built (run __graft_entry__.build())" % path)
+    L = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    P = ctypes.POINTER
+    L.snn_build.argtypes = [i32, i32, P(NeuronParams), P(SynapseParams), ctypes.c_uint64,
+                            i32, vp, P(vp)]
+    L.snn_step.argtypes = [vp, i64]
+    L.snn_read_spikes.argtypes = [vp, vp, vp, i64, P(i64)]
+    L.snn_pending_spikes.argtypes = [vp, P(i64)]
+    L.snn_set_record_capacity.argtypes = [vp, i64]
+    L.snn_read_rates.argtypes = [vp, vp, i64, vp]
+    L.snn_stats.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double), P(i64)]
+    L.snn_get_state.argtypes = [vp, vp, vp, vp]
+    L.snn_read_synapses.argtypes = [vp, i64, i64, vp, vp, vp]
+    L.snn_info.argtypes = [vp, vp, i32]
+    L.snn_step_profiled.argtypes = [vp, i64, vp, vp]
+    L.snn_last_error.argtypes = [vp]
+    L.snn_last_error.restype = ctypes.c_char_p
+    L.snn_destroy.argtypes = [vp]
+    L.snn_destroy.restype = None
+    for f in EXPORTS:
+        if f not in ("snn_last_error", "snn_destroy"):
+            getattr(L, f).restype = i32
+    _lib = L
+    return L
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def neuron_struct(d):
+    return NeuronParams(**{k: d[k] for k, _ in NeuronParams._fields_})
+
+
+def synapse_struct(d):
+    return SynapseParams(**{k: d[k] for k, _ in SynapseParams._fields_})
+
+
+def snn_last_error(handle=None):
+    return load().snn_last_error(handle).decode()
+
+
+def _check(rc, handle, ok=(SNN_OK,)):
+    if rc not in ok:
+        raise SnnError(rc, snn_last_error(handle))
+    return rc
+
+
+def snn_build(grid_w, grid_h, neuron, synapse, seed, precision, stream=None):
+    """Build a net; returns the opaque handle (an int)."""
+    L = load()
+    h = ctypes.c_void_p()
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    n = neuron_struct(neuron)
+    s = synapse_struct(synapse)
+    rc = L.snn_build(int(grid_w), int(grid_h), ctypes.byref(n), ctypes.byref(s),
+                     int(seed), prec, stream, ctypes.byref(h))
+    _check(rc, None)
+    return h.value
+
+
+def snn_step(handle, n_steps):
+    _check(load().snn_step(handle, int(n_steps)), handle)
+
+
+def snn_pending_spikes(handle):
+    n = ctypes.c_int64()
+    _check(load().snn_pending_spikes(handle, ctypes.byref(n)), handle)
+    return n.value
+
+
+def snn_read_spikes(handle, cap=None):
+    """Drain the spike records: (steps, ids, overflowed)."""
+    if cap is None:
+        cap = snn_pending_spikes(handle)
+    st = np.zeros(max(cap, 1), np.int32)
+    ids = np.zeros(max(cap, 1), np.int32)
+    n = ctypes.c_int64()
+    rc = _check(load().snn_read_spikes(handle, _p(st), _p(ids), int(cap), ctypes.byref(n)),
+                handle, ok=(SNN_OK, SNN_EOVERFLOW))
+    return st[:n.value], ids[:n.value], rc == SNN_EOVERFLOW
+
+
+def snn_set_record_capacity(handle, capacity):
+    _check(load().snn_set_record_capacity(handle, int(capacity)), handle)
+
+
+def snn_read_rates(handle, n_cols):
+    hz = np.zeros(2 * n_cols, np.float32)
+    pop = np.zeros(2, np.float32)
+    _check(load().snn_read_rates(handle, _p(hz), hz.size, _p(pop)), handle)
+    return hz.reshape(n_cols, 2), pop
+
+
+def snn_stats(handle):
+    r, e, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(load().snn_stats(handle, ctypes.byref(r), ctypes.byref(e), ctypes.byref(s)), handle)
+    return r.value, e.value, s.value
+
+
+def snn_get_state(handle, n):
+    v = np.zeros(n, np.float32)
+    c = np.zeros(n, np.float32)
+    r = np.zeros(n, np.uint8)
+    _check(load().snn_get_state(handle, _p(v), _p(c), _p(r)), handle)
+    return v, c, r
+
+
+def snn_read_synapses(handle, j0, n, k_out):
+    tgt = np.zeros(n * k_out, np.int64)
+    d = np.zeros(n * k_out, np.int32)
+    w = np.zeros(n * k_out, np.int32)
+    _check(load().snn_read_synapses(handle, int(j0), int(n), _p(tgt), _p(d), _p(w)), handle)
+    sh = (n, k_out)
+    return tgt.reshape(sh), d.reshape(sh), w.reshape(sh)
+
+
+def snn_info(handle):
+    info = np.zeros(6, np.int64)
+    _check(load().snn_info(handle, _p(info), 6), handle)
+    keys = ("neurons", "synapses", "device_bytes", "synapse_bytes", "row_capacity", "precision")
+    return dict(zip(keys, (int(x) for x in info)))
+
+
+def snn_step_profiled(handle, n_steps):
+    """Eager step loop with CUDA events: (ms[update, deliver], bytes[update, deliver])."""
+    ms = np.zeros(2, np.float64)
+    by = np.zeros(2, np.float64)
+    _check(load().snn_step_profiled(handle, int(n_steps), _p(ms), _p(by)), handle)
+    return ms, by
+
+
+def snn_destroy(handle):
+    if handle:
+        load().snn_destroy(handle)
+
+
+class Net:
+    """A grid of cortical columns living on the current CUDA device."""
+
+    def __init__(self, grid_w, grid_h, neuron, synapse, seed, precision="f32w", stream=None):
+        self.grid_w, self.grid_h = grid_w, grid_h
+        self.neuron, self.synapse = dict(neuron), dict(synapse)
+        self.n_cols = grid_w * grid_h
+        self.n = self.n_cols * neuron["n_per_col"]
+        self.k_out = synapse["k_out"]
+        self.handle = snn_build(grid_w, grid_h, neuron, synapse, seed, precision, stream)
+
+    def step(self, n_steps):
+        snn_step(self.handle, n_steps)
+
+    def spikes(self, cap=None):
+        return snn_read_spikes(self.handle, cap)
+
+    def rates(self):
+        return snn_read_rates(self.handle, self.n_cols)
+
+    def stats(self):
+        return snn_stats(self.handle)
+
+    def state(self):
+        return snn_get_state(self.handle, self.n)
+
+    def synapses(self, j0, n):
+        return snn_read_synapses(self.handle, j0, n, self.k_out)
+
+    def info(self):
+        return snn_info(self.handle)
+
+    def set_record_capacity(self, cap):
+        snn_set_record_capacity(self.handle, cap)
+
+    def step_profiled(self, n_steps):
+        return snn_step_profiled(self.handle, n_steps)
+
+    def close(self):
+        if self.handle:
+            snn_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,84 @@
+"""The C-ABI library builds, loads and exports every declared symbol (no GPU).
+
+Only host-side behaviour is exercised here: argument validation happens before
+any CUDA call, so invalid parameters are rejected without a device.
+"""
+import os
+import re
+
+import pytest
+
+from paper_1511_09325_gb300 import build as B
+from paper_1511_09325_gb300 import snn
+from paper_1511_09325_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return snn.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "snn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(snn_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_exports():
+    assert _declared() == sorted(snn.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_library_is_built_for_sm103a():
+    # the fatbin of the in-tree library carries sm_103a code (cuobjdump-free
+    # check: the architecture string the linker records)
+    B.build()
+    data = open(B.LIB, "rb").read()
+    assert b"sm_103a" in data or b"sm_103" in data
+
+
+@pytest.mark.parametrize("field,value", [
+    ("n_per_col", 1), ("n_per_col", 4096), ("n_exc", 2000), ("tau_m", 0.0),
+    ("nu_ext_kHz", 41.0), ("nu_ext_kHz", -1.0), ("theta", float("nan")),
+])
+def test_invalid_neuron_params_rejected(lib, field, value):
+    n = W.neuron_params(**{field: value})
+    with pytest.raises(snn.SnnError) as e:
+        snn.snn_build(2, 2, n, W.synapse_params(), 1, "f32w")
+    assert e.value.code == snn.SNN_EINVAL
+    assert snn.snn_last_error()
+
+
+@pytest.mark.parametrize("field,value", [
+    ("k_out", 0), ("k_out", 4000), ("stencil_radius", 4), ("d_min", 0), ("d_max", 33),
+    ("frac_local", 1.5), ("periodic", 0), ("lambda_cols", 0.0),
+])
+def test_invalid_synapse_params_rejected(lib, field, value):
+    s = W.synapse_params(**{field: value})
+    with pytest.raises(snn.SnnError) as e:
+        snn.snn_build(2, 2, W.neuron_params(), s, 1, "f32w")
+    assert e.value.code == snn.SNN_EINVAL
+
+
+def test_invalid_grid_and_precision_rejected(lib):
+    for gw, gh, prec in ((0, 2, 0), (2, -1, 0), (2, 2, 7)):
+        with pytest.raises(snn.SnnError) as e:
+            snn.snn_build(gw, gh, W.neuron_params(), W.synapse_params(), 1, prec)
+        assert e.value.code == snn.SNN_EINVAL
+
+
+def test_destroy_null_is_noop(lib):
+    lib.snn_destroy(None)
+
+
+def test_calls_on_null_net_fail_cleanly(lib):
+    assert lib.snn_step(None, 1) == snn.SNN_EINVAL
+    assert lib.snn_stats(None, None, None, None) == snn.SNN_EINVAL
+    assert lib.snn_last_error(None) is not None
