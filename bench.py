@@ -38,8 +38,10 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 96x96 FP16-vs-FP32 comparison")
-    ap.add_argument("--profile-steps", type=int, default=2000)
+    ap.add_argument("--profile-steps", type=int, default=None,
+                    help="steps of the per-kernel timing pass (default: all timed steps)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     return ap.parse_args()
 
 
@@ -161,17 +163,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _measure_net(snn, torch, cfg, seed, steps, warmup, stream):
-    """Build a net, warm it up, time `steps` graph-replayed steps."""
+def _build_net(snn, torch, cfg, seed, stream):
     n, s = W.neuron_params(), W.synapse_params()
     t0 = time.perf_counter()
     net = snn.Net(cfg["grid_w"], cfg["grid_h"], n, s, seed, cfg["precision"],
                   stream=stream.cuda_stream)
     torch.cuda.synchronize()
-    build_s = time.perf_counter() - t0
-    net.step(warmup)
-    net.spikes()
+    return net, time.perf_counter() - t0
+
+
+def _timed(net, torch, stream, steps, barrier=None):
+    """Device time of `steps` graph-replayed steps, barrier + sync on both sides."""
     torch.cuda.synchronize()
+    if barrier:
+        barrier()
     r0, e0, _ = net.stats()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -179,9 +184,53 @@ def _measure_net(snn, torch, cfg, seed, steps, warmup, stream):
     net.step(steps)
     ev1.record(stream)
     torch.cuda.synchronize()
+    if barrier:
+        barrier()
     ms = ev0.elapsed_time(ev1)
     r1, e1, _ = net.stats()
-    return net, build_s, ms, r1 - r0, e1 - e0
+    return ms, r1 - r0, e1 - e0
+
+
+def _kernel_roofline(snn, torch, cfg, seed, stream, warmup, P, workload):
+    """Per-kernel device time and algorithmic bytes over the timed window.
+
+    A second net with the same seed replays the identical window (the
+    simulation is deterministic) with every kernel bracketed by CUDA events
+    on the net's stream."""
+    twin, _ = _build_net(snn, torch, cfg, seed, stream)
+    twin.step(warmup)
+    kms, kbytes = twin.step_profiled(P)
+    twin.close()
+    hbm, peak_kind = _peaks()
+    dom = 0 if kms[0] >= kms[1] else 1
+    kname = ["update_kernel", "deliver_kernel"][dom]
+    achieved = kbytes[dom] / (kms[dom] * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+            "traffic": _traffic(workload, kname), "launches": P,
+            "kernel_ms": {"update": kms[0] / P, "deliver": kms[1] / P},
+            "kernel_gbs": {"update": kbytes[0] / (kms[0] * 1e-3) / 1e9,
+                           "deliver": kbytes[1] / (kms[1] * 1e-3) / 1e9},
+            "algorithmic_bytes_per_launch": {"update": kbytes[0] / P, "deliver": kbytes[1] / P}}
+
+
+def _e2e(net, torch, E, ws):
+    """Same metric through the public API with host buffers: every step is
+    one snn_step call followed by a drain of that step's spike records to
+    host memory (device -> host copy and stream sync inside the region)."""
+    net.spikes()
+    torch.cuda.synchronize()
+    r0, _, _ = net.stats()
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(E):
+        net.step(1)
+        st, _, _ = net.spikes()
+        d2h += 8 * len(st) + 48  # records, plus the control block read
+    dt = time.perf_counter() - t0
+    r1, _, _ = net.stats()
+    return {"value": (r1 - r0) * ws / dt, "unit": UNIT, "h2d_bytes_per_step": 0,
+            "d2h_bytes_per_step": d2h / E, "steps": E}
 
 
 def run_ours(args):
@@ -191,6 +240,7 @@ def run_ours(args):
     from paper_1511_09325_gb300 import snn
 
     ws, rank, local = _dist()
+    dist = None
     if ws > 1:
         import torch.distributed as dist
 
@@ -198,13 +248,12 @@ def run_ours(args):
         dist.init_process_group("nccl")
     else:
         torch.cuda.set_device(0)
-    if rank == 0 or ws == 1:
+    if rank == 0:
         B.build()
-    if ws > 1:
+    if dist:
         dist.barrier()
     snn.load()
-    dev = torch.cuda.current_device()
-    props = torch.cuda.get_device_properties(dev)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
     uuid = str(getattr(props, "uuid", "") or "")
     if uuid and not uuid.startswith("GPU-"):
         uuid = "GPU-" + uuid
@@ -215,91 +264,62 @@ def run_ours(args):
 
     clocks = Clocks(uuid)
     clocks.start()
-    net, build_s, ms, rec_ev, ext_ev = _measure_net(snn, torch, cfg, seed, K, Wm, stream)
-    if ws > 1:
+    net, build_s = _build_net(snn, torch, cfg, seed, stream)
+    net.step(Wm)
+    net.spikes()
+    ms, rec_ev, ext_ev = _timed(net, torch, stream, K, dist.barrier if dist else None)
+    clk = clocks.stop()
+    if dist:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         ev = torch.tensor([rec_ev, ext_ev], device="cuda", dtype=torch.float64)
         dist.all_reduce(ev)
         rec_ev, ext_ev = float(ev[0].item()), float(ev[1].item())
-    clk = clocks.stop()
     info = net.info()
     _, pop_hz = net.rates()
-
-    # per-kernel device time over the same kind of steps (eager launches)
-    P = min(args.profile_steps, max(K, 1))
-    kms, kbytes = net.step_profiled(P)
-    hbm, peak_kind = _peaks()
-    dom = 0 if kms[0] >= kms[1] else 1
-    kname = ["update_kernel", "deliver_kernel"][dom]
-    achieved = kbytes[dom] / (kms[dom] * 1e-3) / 1e9
-    tr = _traffic(args.workload, kname)
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-                "traffic": tr, "launches": P,
-                "kernel_ms": {"update": kms[0] / P, "deliver": kms[1] / P},
-                "kernel_gbs": {"update": kbytes[0] / (kms[0] * 1e-3) / 1e9,
-                               "deliver": kbytes[1] / (kms[1] * 1e-3) / 1e9}}
-
-    # end to end through the public API: step, then drain the step's spikes
-    # to pinned-free host arrays (device -> host copy inside the timed region)
-    net.spikes()
-    torch.cuda.synchronize()
-    E = min(args.e2e_steps, max(K, 1))
-    r0, _, _ = net.stats()
-    d2h = 0
-    t0 = time.perf_counter()
-    for _ in range(E):
-        net.step(1)
-        st, ids, _ = net.spikes()
-        d2h += 8 * len(st) + 40  # records plus the control block read
-    e2e_s = time.perf_counter() - t0
-    r1, _, _ = net.stats()
-    e2e = {"value": (r1 - r0) * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
-           "d2h_bytes_per_step": d2h / E, "steps": E}
+    e2e = _e2e(net, torch, max(1, min(args.e2e_steps, max(K, 1))), ws)
     net.close()
+    P = K if args.profile_steps is None else min(args.profile_steps, K)
+    roofline = _kernel_roofline(snn, torch, cfg, seed, stream, Wm, max(1, P), args.workload)
 
     extra = None
-    if not args.no_extra and ws == 1 and rank == 0:
+    if not args.no_extra and ws == 1:
         extra = _precision_form(snn, torch, stream, Wm)
-
     cpu = None
-    if rank == 0 and ws == 1:
+    if ws == 1 and not args.no_cpu:
         cb = _cpu_baseline(args.workload)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
-    if ws > 1:
+    if dist:
         dist.barrier()
-    if rank != 0:
-        if ws > 1:
-            dist.destroy_process_group()
-        return
-    value = rec_ev / (ms * 1e-3)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
-        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+i32" if cfg["precision"] == "f32w" else "f16+i32",
-        "data": "synthetic",
-        "config": {"workload": args.workload, "grid": [cfg["grid_w"], cfg["grid_h"]],
-                   "neurons": info["neurons"], "synapses": info["synapses"],
-                   "precision": cfg["precision"], "seed": cfg["seed"],
-                   "parallelism": "replicas%d" % ws,
-                   "l2": "inputs larger than L2 (synapse table %.1f GB)" % (info["synapse_bytes"] / 1e9)},
-        "wall_s_per_model_s": (ms / K),
-        "paper_convention_events_per_s": (rec_ev + ext_ev) / (ms * 1e-3),
-        "pop_rates_hz": [float(pop_hz[0]), float(pop_hz[1])],
-        "build_s": build_s,
-        "gpu_launches": 2 * K,
-        "roofline": roofline,
-        "e2e": e2e,
-        "clocks": clk,
-        "cpu_baseline": cpu,
-    }
-    if extra:
-        line["precision_form"] = extra
-    print(json.dumps(line), flush=True)
-    if ws > 1:
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": rec_ev / (ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+            "steps": K, "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+i32" if cfg["precision"] == "f32w" else "f16+i32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "grid": [cfg["grid_w"], cfg["grid_h"]],
+                       "neurons": info["neurons"], "synapses": info["synapses"],
+                       "precision": cfg["precision"], "seed": cfg["seed"],
+                       "parallelism": "replicas%d" % ws,
+                       "l2": "inputs larger than L2 (synapse table %.1f GB)"
+                             % (info["synapse_bytes"] / 1e9)},
+            "wall_s_per_model_s": ms / K,
+            "paper_convention_events_per_s": (rec_ev + ext_ev) / (ms * 1e-3),
+            "pop_rates_hz": [float(pop_hz[0]), float(pop_hz[1])],
+            "build_s": build_s,
+            "gpu_launches": 2 * K,
+            "roofline": roofline,
+            "e2e": e2e,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        if extra:
+            line["precision_form"] = extra
+        print(json.dumps(line), flush=True)
+    if dist:
         dist.destroy_process_group()
 
 
@@ -313,8 +333,10 @@ def _precision_form(snn, torch, stream, warmup, steps=1000):
         if need > free * 0.97:
             out[prec] = {"skipped": "needs %.0f GB of %.0f GB free" % (need / 1e9, free / 1e9)}
             continue
-        net, build_s, ms, rec_ev, ext_ev = _measure_net(snn, torch, cfg, cfg["seed"], steps,
-                                                        warmup, stream)
+        net, build_s = _build_net(snn, torch, cfg, cfg["seed"], stream)
+        net.step(warmup)
+        net.spikes()
+        ms, rec_ev, ext_ev = _timed(net, torch, stream, steps)
         _, pop = net.rates()
         kms, kb = net.step_profiled(min(steps, 500))
         hbm, _ = _peaks()

@@ -14,7 +14,7 @@ using namespace snn;
 struct snn_net {
   // configuration
   int W = 0, H = 0, npc = 0, nexc = 0, K = 0, dmin = 0, ndel = 0, nslot = 0;
-  int precision = 0, rowcap = 0, rec_size = 0, num_sms = 0, deliver_grid = 0;
+  int precision = 0, rowcap = 0, rec_size = 0, num_sms = 0, split = 1, update_grid = 0;
   long long N = 0, Npad = 0, ncol = 0;
   uint64_t seed = 0;
   HostTables tables;
@@ -27,10 +27,12 @@ struct snn_net {
   uint8_t* R = nullptr;
   int32_t* acc = nullptr;
   uint32_t* ids = nullptr;
+  unsigned* cnt = nullptr;
   Ctl* ctl = nullptr;
   unsigned long long* rec = nullptr;
   long long rec_cap = 0;
   unsigned long long* colcnt = nullptr;
+  unsigned long long* ext_part = nullptr;
   size_t device_bytes = 0;
   // execution
   cudaStream_t stream = nullptr;
@@ -88,7 +90,7 @@ void free_graphs(snn_net* net) {
 void release(snn_net* net) {
   free_graphs(net);
   void* ptrs[] = {net->syn, net->bend, net->V, net->C, net->R, net->acc,
-                  net->ids, net->ctl, net->rec, net->colcnt};
+                  net->ids, net->cnt, net->ctl, net->rec, net->colcnt, net->ext_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
@@ -133,8 +135,8 @@ int capture(snn_net* net, int steps, cudaGraphExec_t* out) {
   SNN_CUDA(net, cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
   for (int s = 0; s < steps && le == cudaSuccess; ++s) {
-    le = launch_update(net->sp, net->stream);
-    if (le == cudaSuccess) le = launch_deliver(net->sp, net->precision, net->deliver_grid, net->stream);
+    le = launch_update(net->sp, net->update_grid, net->stream);
+    if (le == cudaSuccess) le = launch_deliver(net->sp, net->precision, net->stream);
   }
   cudaError_t ee = cudaStreamEndCapture(net->stream, &g);
   if (le != cudaSuccess) {
@@ -161,6 +163,8 @@ void fill_step_params(snn_net* net) {
   p.ndel = net->ndel;
   p.nslot = net->nslot;
   p.rowcap = net->rowcap;
+  p.ncol = (int)net->ncol;
+  p.split = net->split;
   p.seed_lo = (uint32_t)(net->seed & 0xFFFFFFFFu);
   p.seed_hi = (uint32_t)(net->seed >> 32);
   p.pvv = t.pvv;
@@ -177,12 +181,14 @@ void fill_step_params(snn_net* net) {
   p.R = net->R;
   p.acc = net->acc;
   p.ids = net->ids;
+  p.cnt = net->cnt;
   p.bend = net->bend;
   p.syn = net->syn;
   p.ctl = net->ctl;
   p.rec = net->rec;
   p.rec_cap = net->rec_cap;
   p.colcnt = net->colcnt;
+  p.ext_part = net->ext_part;
 }
 
 int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
@@ -215,6 +221,7 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   int dev = 0;
   SNN_CUDA(net, cudaGetDevice(&dev));
   SNN_CUDA(net, cudaDeviceGetAttribute(&net->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  net->split = deliver_split(net->ncol, net->num_sms);
 
   const size_t syn_bytes = (size_t)net->N * net->rowcap * net->rec_size;
   if ((rc = dalloc(net, &net->syn, syn_bytes))) return rc;
@@ -224,9 +231,12 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if ((rc = dalloc(net, &net->R, (size_t)net->Npad))) return rc;
   if ((rc = dalloc(net, &net->acc, (size_t)net->Npad * 4))) return rc;
   if ((rc = dalloc(net, &net->ids, (size_t)net->nslot * net->N * 4))) return rc;
+  if ((rc = dalloc(net, &net->cnt, (size_t)net->nslot * net->ncol * 4))) return rc;
   if ((rc = dalloc(net, &net->ctl, sizeof(Ctl)))) return rc;
   if ((rc = dalloc(net, &net->rec, (size_t)net->rec_cap * 8))) return rc;
   if ((rc = dalloc(net, &net->colcnt, (size_t)net->ncol * 2 * 8))) return rc;
+  net->update_grid = update_grid(net->N, net->num_sms);
+  if ((rc = dalloc(net, &net->ext_part, (size_t)net->update_grid * 8))) return rc;
   uint32_t* wtab = nullptr;
   if ((rc = dalloc(net, &wtab, net->tables.wtab.size() * 4))) return rc;
   net->device_bytes -= net->tables.wtab.size() * 4;
@@ -234,7 +244,10 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   cudaError_t e = cudaMemcpyAsync(wtab, net->tables.wtab.data(), net->tables.wtab.size() * 4,
                                   cudaMemcpyHostToDevice, net->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(net->ctl, 0, sizeof(Ctl), net->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(net->cnt, 0, (size_t)net->nslot * net->ncol * 4, net->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(net->colcnt, 0, (size_t)net->ncol * 16, net->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(net->ext_part, 0, (size_t)net->update_grid * 8, net->stream);
   if (e == cudaSuccess) {
     BuildParams bp{};
     bp.N = net->N;
@@ -263,7 +276,6 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
   cudaFree(wtab);
   if (e != cudaSuccess) return cuda_fail(net, e, "network construction");
-  net->deliver_grid = deliver_grid(precision, net->num_sms);
   return SNN_OK;
 }
 
@@ -349,9 +361,9 @@ int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes) 
     e = cudaMemcpyAsync(hspk, (char*)net->ctl + off_spk, 8, cudaMemcpyDeviceToHost, net->stream);
   for (int64_t s = 0; s < n_steps && e == cudaSuccess; ++s) {
     e = cudaEventRecord(ev[3 * s], net->stream);
-    if (e == cudaSuccess) e = launch_update(net->sp, net->stream);
+    if (e == cudaSuccess) e = launch_update(net->sp, net->update_grid, net->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], net->stream);
-    if (e == cudaSuccess) e = launch_deliver(net->sp, net->precision, net->deliver_grid, net->stream);
+    if (e == cudaSuccess) e = launch_deliver(net->sp, net->precision, net->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], net->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(hspk + s + 1, (char*)net->ctl + off_spk, 8, cudaMemcpyDeviceToHost,
@@ -492,8 +504,14 @@ int snn_stats(snn_net* net, double* recurrent_events, double* external_events, i
   cudaError_t e;
   Ctl c = read_ctl(net, &e);
   if (e != cudaSuccess) return cuda_fail(net, e, "read control block");
+  std::vector<unsigned long long> part((size_t)net->update_grid);
+  SNN_CUDA(net, cudaMemcpyAsync(part.data(), net->ext_part, part.size() * 8, cudaMemcpyDeviceToHost,
+                                net->stream));
+  SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+  unsigned long long ext = 0ull;
+  for (unsigned long long v : part) ext += v;
   if (recurrent_events) *recurrent_events = (double)c.spikes * (double)net->K;
-  if (external_events) *external_events = (double)c.ext_events;
+  if (external_events) *external_events = (double)ext;
   if (steps) *steps = (int64_t)c.t;
   return SNN_OK;
 }

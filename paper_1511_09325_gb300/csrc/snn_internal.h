@@ -16,10 +16,13 @@
 //   V, C   float[Npad] membrane potential (mV) and calcium.
 //   R      u8[Npad] remaining refractory steps.
 //   acc    int32[Npad] recurrent input of the next step, 2^-16 mV units.
-//   ids    u32[d_max][N] spike lists of the last d_max steps (slot t % d_max).
-//   ctl    control block (step counter, per-slot spike counts, totals).
+//   ids    u32[d_max][N] spike lists of the last d_max steps (slot t % d_max);
+//          column c's spikes of a step occupy [c * n_per_col, + cnt[slot][c]).
+//   cnt    u32[d_max][ncol] spikes per column of each slot's step.
+//   ctl    control block (step counter, record counter, totals).
 //   rec    u64 spike records (step << 32 | id), drained by snn_read_spikes.
 //   colcnt u64[ncol][2] spike counts per column and population.
+//   ext_part u64[update grid] external-event counts summed by each update block.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -64,11 +67,9 @@ int make_host_tables(const snn_neuron_params& np, const snn_synapse_params& sp,
 // Device control block.
 struct Ctl {
   long long t;                          // step index of the next update
-  unsigned int count[kMaxDelays];       // spikes emitted by the step in slot s
   unsigned long long rec_count;         // records appended since the last drain
   unsigned int rec_overflow;            // set when a record did not fit
   unsigned int done;                    // delivery blocks finished this step
-  unsigned long long ext_events;        // sum of external Poisson counts
   unsigned long long spikes;            // spikes since build
 };
 
@@ -76,6 +77,7 @@ struct Ctl {
 struct StepParams {
   long long N;
   int npc, nexc, W, H, K, dmin, ndel, nslot, rowcap;
+  int ncol, split;  // columns; delivery blocks per source column
   uint32_t seed_lo, seed_hi;
   float theta, vr, dc, pvv, pcc, pvc_e, pvc_i;
   int32_t jx;
@@ -88,12 +90,14 @@ struct StepParams {
   uint8_t* R;
   int32_t* acc;
   uint32_t* ids;
+  unsigned* cnt;
   const uint8_t* bend;
   const void* syn;
   Ctl* ctl;
   unsigned long long* rec;
   long long rec_cap;
   unsigned long long* colcnt;
+  unsigned long long* ext_part;  // external-event partial sums, one per update block
 };
 
 struct BuildParams {
@@ -111,9 +115,9 @@ struct BuildParams {
 cudaError_t launch_build(const BuildParams& bp, int precision, int num_sms,
                          cudaStream_t st);
 cudaError_t launch_init_state(const StepParams& p, cudaStream_t st);
-cudaError_t launch_update(const StepParams& p, cudaStream_t st);
-cudaError_t launch_deliver(const StepParams& p, int precision, int grid,
-                           cudaStream_t st);
-int deliver_grid(int precision, int num_sms);
+cudaError_t launch_update(const StepParams& p, int grid, cudaStream_t st);
+int update_grid(long long N, int num_sms);
+cudaError_t launch_deliver(const StepParams& p, int precision, cudaStream_t st);
+int deliver_split(long long ncol, int num_sms);
 
 }  // namespace snn

@@ -50,8 +50,12 @@ SYNAPSE = dict(
 WORKLOADS = {
     # 2x2 columns, 4960 neurons, 6.15 M synapses: the parity case.
     "cols2x2_f32w": dict(grid_w=2, grid_h=2, seed=1, precision="f32w", steps=1000),
+    # 12x12 columns, 178 560 neurons, 221.4 M synapses: a profiling-size case.
+    "cols12x12_f32w": dict(grid_w=12, grid_h=12, seed=2, precision="f32w", steps=1000),
+    "cols12x12_f16w": dict(grid_w=12, grid_h=12, seed=2, precision="f16w", steps=1000),
     # 24x24 columns, 714 240 neurons, 885.7 M synapses (Sec. 2, Table 1).
     "cols24x24_f32w": dict(grid_w=24, grid_h=24, seed=2, precision="f32w", steps=10000),
+    "cols24x24_f16w": dict(grid_w=24, grid_h=24, seed=2, precision="f16w", steps=10000),
     # 48x48 columns, 2.86 M neurons, 3.54 G synapses (Table 1).
     "cols48x48_f32w": dict(grid_w=48, grid_h=48, seed=3, precision="f32w", steps=10000),
     "cols48x48_f16w": dict(grid_w=48, grid_h=48, seed=3, precision="f16w", steps=10000),
