@@ -1,7 +1,9 @@
 // snn_api.cu -- the C ABI: net lifetime, graph-captured step loop, readback.
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
@@ -14,7 +16,9 @@ using namespace snn;
 struct snn_net {
   // configuration
   int W = 0, H = 0, npc = 0, nexc = 0, K = 0, dmin = 0, ndel = 0, nslot = 0;
-  int precision = 0, rowcap = 0, rec_size = 0, num_sms = 0, split = 1, update_grid = 0;
+  int precision = 0, rowcap = 0, rec_size = 0, num_sms = 0, update_grid = 0;
+  bool agg = true;
+  int deliver_grid = 0;
   long long N = 0, Npad = 0, ncol = 0;
   uint64_t seed = 0;
   HostTables tables;
@@ -30,9 +34,12 @@ struct snn_net {
   unsigned* cnt = nullptr;
   Ctl* ctl = nullptr;
   unsigned long long* rec = nullptr;
-  long long rec_cap = 0;
+  long long rec_cap = 0;     // requested total record capacity
+  long long rec_region = 0;  // records per update block
+  unsigned long long* rcnt = nullptr;
   unsigned long long* colcnt = nullptr;
   unsigned long long* ext_part = nullptr;
+  unsigned long long* spk_part = nullptr;
   size_t device_bytes = 0;
   // execution
   cudaStream_t stream = nullptr;
@@ -90,7 +97,8 @@ void free_graphs(snn_net* net) {
 void release(snn_net* net) {
   free_graphs(net);
   void* ptrs[] = {net->syn, net->bend, net->V, net->C, net->R, net->acc,
-                  net->ids, net->cnt, net->ctl, net->rec, net->colcnt, net->ext_part};
+                  net->ids, net->cnt, net->ctl, net->rec, net->rcnt, net->colcnt,
+                  net->ext_part, net->spk_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
@@ -136,7 +144,7 @@ int capture(snn_net* net, int steps, cudaGraphExec_t* out) {
   cudaError_t le = cudaSuccess;
   for (int s = 0; s < steps && le == cudaSuccess; ++s) {
     le = launch_update(net->sp, net->update_grid, net->stream);
-    if (le == cudaSuccess) le = launch_deliver(net->sp, net->precision, net->stream);
+    if (le == cudaSuccess) le = launch_deliver(net->sp, net->precision, net->deliver_grid, net->stream);
   }
   cudaError_t ee = cudaStreamEndCapture(net->stream, &g);
   if (le != cudaSuccess) {
@@ -164,7 +172,7 @@ void fill_step_params(snn_net* net) {
   p.nslot = net->nslot;
   p.rowcap = net->rowcap;
   p.ncol = (int)net->ncol;
-  p.split = net->split;
+  p.agg = net->agg ? 1 : 0;
   p.seed_lo = (uint32_t)(net->seed & 0xFFFFFFFFu);
   p.seed_hi = (uint32_t)(net->seed >> 32);
   p.pvv = t.pvv;
@@ -186,9 +194,11 @@ void fill_step_params(snn_net* net) {
   p.syn = net->syn;
   p.ctl = net->ctl;
   p.rec = net->rec;
-  p.rec_cap = net->rec_cap;
+  p.rec_region = net->rec_region;
+  p.rcnt = net->rcnt;
   p.colcnt = net->colcnt;
   p.ext_part = net->ext_part;
+  p.spk_part = net->spk_part;
 }
 
 int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
@@ -203,7 +213,7 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   net->K = sp->k_out;
   net->dmin = sp->d_min;
   net->ndel = sp->d_max - sp->d_min + 1;
-  net->nslot = sp->d_max;
+  net->nslot = sp->d_max + 1;
   net->precision = precision;
   net->seed = seed;
   net->ncol = (long long)gw * gh;
@@ -221,7 +231,9 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   int dev = 0;
   SNN_CUDA(net, cudaGetDevice(&dev));
   SNN_CUDA(net, cudaDeviceGetAttribute(&net->num_sms, cudaDevAttrMultiProcessorCount, dev));
-  net->split = deliver_split(net->ncol, net->num_sms);
+  net->update_grid = update_grid(net->N, net->num_sms);
+  net->deliver_grid = deliver_grid(precision, net->num_sms, net->npc, net->agg);
+  net->rec_region = (net->rec_cap + net->update_grid - 1) / net->update_grid;
 
   const size_t syn_bytes = (size_t)net->N * net->rowcap * net->rec_size;
   if ((rc = dalloc(net, &net->syn, syn_bytes))) return rc;
@@ -231,12 +243,13 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if ((rc = dalloc(net, &net->R, (size_t)net->Npad))) return rc;
   if ((rc = dalloc(net, &net->acc, (size_t)net->Npad * 4))) return rc;
   if ((rc = dalloc(net, &net->ids, (size_t)net->nslot * net->N * 4))) return rc;
-  if ((rc = dalloc(net, &net->cnt, (size_t)net->nslot * net->ncol * 4))) return rc;
+  if ((rc = dalloc(net, &net->cnt, (size_t)net->nslot * 4))) return rc;
   if ((rc = dalloc(net, &net->ctl, sizeof(Ctl)))) return rc;
-  if ((rc = dalloc(net, &net->rec, (size_t)net->rec_cap * 8))) return rc;
+  if ((rc = dalloc(net, &net->rec, (size_t)net->rec_region * net->update_grid * 8))) return rc;
+  if ((rc = dalloc(net, &net->rcnt, (size_t)net->update_grid * 8))) return rc;
   if ((rc = dalloc(net, &net->colcnt, (size_t)net->ncol * 2 * 8))) return rc;
-  net->update_grid = update_grid(net->N, net->num_sms);
   if ((rc = dalloc(net, &net->ext_part, (size_t)net->update_grid * 8))) return rc;
+  if ((rc = dalloc(net, &net->spk_part, (size_t)net->update_grid * 8))) return rc;
   uint32_t* wtab = nullptr;
   if ((rc = dalloc(net, &wtab, net->tables.wtab.size() * 4))) return rc;
   net->device_bytes -= net->tables.wtab.size() * 4;
@@ -245,9 +258,11 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
                                   cudaMemcpyHostToDevice, net->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(net->ctl, 0, sizeof(Ctl), net->stream);
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(net->cnt, 0, (size_t)net->nslot * net->ncol * 4, net->stream);
+    e = cudaMemsetAsync(net->cnt, 0, (size_t)net->nslot * 4, net->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(net->colcnt, 0, (size_t)net->ncol * 16, net->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(net->ext_part, 0, (size_t)net->update_grid * 8, net->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(net->spk_part, 0, (size_t)net->update_grid * 8, net->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(net->rcnt, 0, (size_t)net->update_grid * 8, net->stream);
   if (e == cudaSuccess) {
     BuildParams bp{};
     bp.N = net->N;
@@ -348,27 +363,28 @@ int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes) 
   if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
   if (n_steps < 0) return fail(net, SNN_EINVAL, "n_steps must be >= 0");
   std::vector<cudaEvent_t> ev((size_t)n_steps * 3 + 1);
-  std::vector<unsigned long long> spikes((size_t)n_steps + 1, 0ull);
-  unsigned long long* hspk = nullptr;
-  SNN_CUDA(net, cudaMallocHost(&hspk, ((size_t)n_steps + 1) * 8));
-  int rc = SNN_OK;
+  unsigned long long* dspk = nullptr;  // spikes so far, after each step
+  int rc = dalloc(net, &dspk, ((size_t)n_steps + 1) * 8);
+  if (rc) return rc;
+  net->device_bytes -= ((size_t)n_steps + 1) * 8;
+  std::vector<unsigned long long> hspk((size_t)n_steps + 1, 0ull);
   size_t made = 0;
   cudaError_t e = cudaSuccess;
   for (; made < ev.size() && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
   if (e != cudaSuccess) --made;
-  const size_t off_spk = offsetof(Ctl, spikes);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(hspk, (char*)net->ctl + off_spk, 8, cudaMemcpyDeviceToHost, net->stream);
+  if (e == cudaSuccess) e = launch_sum_parts(net->spk_part, net->update_grid, dspk, net->stream);
   for (int64_t s = 0; s < n_steps && e == cudaSuccess; ++s) {
     e = cudaEventRecord(ev[3 * s], net->stream);
     if (e == cudaSuccess) e = launch_update(net->sp, net->update_grid, net->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], net->stream);
-    if (e == cudaSuccess) e = launch_deliver(net->sp, net->precision, net->stream);
+    if (e == cudaSuccess)
+      e = launch_deliver(net->sp, net->precision, net->deliver_grid, net->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], net->stream);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(hspk + s + 1, (char*)net->ctl + off_spk, 8, cudaMemcpyDeviceToHost,
-                          net->stream);
+      e = launch_sum_parts(net->spk_part, net->update_grid, dspk + s + 1, net->stream);
   }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hspk.data(), dspk, hspk.size() * 8, cudaMemcpyDeviceToHost, net->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
   double t_up = 0.0, t_dl = 0.0, b_up = 0.0, b_dl = 0.0;
   if (e == cudaSuccess) {
@@ -387,7 +403,7 @@ int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes) 
     rc = cuda_fail(net, e, "profiled step");
   }
   for (size_t i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
-  cudaFreeHost(hspk);
+  cudaFree(dspk);
   if (rc == SNN_OK) {
     if (ms) {
       ms[0] = t_up;
@@ -401,12 +417,46 @@ int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes) 
   return rc;
 }
 
+namespace {
+
+// Records per region since the last drain, and the number kept.
+int record_counts(snn_net* net, std::vector<unsigned long long>* cnt, long long* kept,
+                  bool* lost) {
+  cnt->assign((size_t)net->update_grid, 0ull);
+  Ctl c{};
+  SNN_CUDA(net, cudaMemcpyAsync(cnt->data(), net->rcnt, cnt->size() * 8, cudaMemcpyDeviceToHost,
+                                net->stream));
+  SNN_CUDA(net, cudaMemcpyAsync(&c, net->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, net->stream));
+  SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+  *kept = 0;
+  *lost = c.rec_overflow != 0u;
+  for (unsigned long long v : *cnt) {
+    const long long k = (long long)v < net->rec_region ? (long long)v : net->rec_region;
+    *kept += k;
+    if ((long long)v > net->rec_region) *lost = true;
+  }
+  return SNN_OK;
+}
+
+int reset_records(snn_net* net) {
+  const unsigned zero32 = 0u;
+  SNN_CUDA(net, cudaMemsetAsync(net->rcnt, 0, (size_t)net->update_grid * 8, net->stream));
+  SNN_CUDA(net, cudaMemcpyAsync((char*)net->ctl + offsetof(Ctl, rec_overflow), &zero32, 4,
+                                cudaMemcpyHostToDevice, net->stream));
+  SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+  return SNN_OK;
+}
+
+}  // namespace
+
 int snn_pending_spikes(snn_net* net, int64_t* n_out) {
   if (!net || !n_out) return fail(net, SNN_EINVAL, "null argument");
-  cudaError_t e;
-  Ctl c = read_ctl(net, &e);
-  if (e != cudaSuccess) return cuda_fail(net, e, "read control block");
-  *n_out = (int64_t)(c.rec_count < (unsigned long long)net->rec_cap ? c.rec_count : net->rec_cap);
+  std::vector<unsigned long long> cnt;
+  long long kept = 0;
+  bool lost = false;
+  int rc = record_counts(net, &cnt, &kept, &lost);
+  if (rc) return rc;
+  *n_out = kept;
   return SNN_OK;
 }
 
@@ -414,31 +464,42 @@ int snn_read_spikes(snn_net* net, int32_t* steps, int32_t* ids, int64_t cap, int
   if (!net || !n_out || cap < 0 || (cap > 0 && (!steps || !ids)))
     return fail(net, SNN_EINVAL, "bad argument");
   *n_out = 0;
-  cudaError_t e;
-  Ctl c = read_ctl(net, &e);
-  if (e != cudaSuccess) return cuda_fail(net, e, "read control block");
-  const long long kept = (long long)(c.rec_count < (unsigned long long)net->rec_cap ? c.rec_count
-                                                                                  : net->rec_cap);
-  const long long n = kept < cap ? kept : cap;
-  bool lost = c.rec_overflow != 0u || kept > cap;
-  if (n > 0) {
-    std::vector<unsigned long long> h((size_t)n);
-    SNN_CUDA(net, cudaMemcpyAsync(h.data(), net->rec, (size_t)n * 8, cudaMemcpyDeviceToHost, net->stream));
-    SNN_CUDA(net, cudaStreamSynchronize(net->stream));
-    // records of one step are contiguous and steps appear in order
-    for (long long k = 0; k < n; ++k) {
-      steps[k] = (int32_t)(h[k] >> 32);
-      ids[k] = (int32_t)(h[k] & 0xFFFFFFFFull);
+  std::vector<unsigned long long> cnt;
+  long long kept = 0;
+  bool lost = false;
+  int rc = record_counts(net, &cnt, &kept, &lost);
+  if (rc) return rc;
+  if (kept > 0) {
+    // copy the used part of every region (one strided copy), then merge:
+    // each region is in step order, so a sort of (step << 32 | id) puts the
+    // whole window in step order
+    long long width = 0;
+    for (unsigned long long v : cnt) {
+      const long long k = (long long)v < net->rec_region ? (long long)v : net->rec_region;
+      if (k > width) width = k;
     }
+    std::vector<unsigned long long> h((size_t)width * net->update_grid);
+    SNN_CUDA(net, cudaMemcpy2DAsync(h.data(), (size_t)width * 8, net->rec,
+                                    (size_t)net->rec_region * 8, (size_t)width * 8,
+                                    (size_t)net->update_grid, cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+    std::vector<unsigned long long> all;
+    all.reserve((size_t)kept);
+    for (int b = 0; b < net->update_grid; ++b) {
+      const long long k = (long long)cnt[b] < net->rec_region ? (long long)cnt[b] : net->rec_region;
+      all.insert(all.end(), h.begin() + (size_t)b * width, h.begin() + (size_t)b * width + k);
+    }
+    std::sort(all.begin(), all.end());
+    const long long n = kept < cap ? kept : cap;
+    if (kept > cap) lost = true;
+    for (long long k = 0; k < n; ++k) {
+      steps[k] = (int32_t)(all[k] >> 32);
+      ids[k] = (int32_t)(all[k] & 0xFFFFFFFFull);
+    }
+    *n_out = n;
   }
-  const unsigned long long zero = 0ull;
-  const unsigned zero32 = 0u;
-  SNN_CUDA(net, cudaMemcpyAsync((char*)net->ctl + offsetof(Ctl, rec_count), &zero, 8,
-                                cudaMemcpyHostToDevice, net->stream));
-  SNN_CUDA(net, cudaMemcpyAsync((char*)net->ctl + offsetof(Ctl, rec_overflow), &zero32, 4,
-                                cudaMemcpyHostToDevice, net->stream));
-  SNN_CUDA(net, cudaStreamSynchronize(net->stream));
-  *n_out = n;
+  rc = reset_records(net);
+  if (rc) return rc;
   if (lost) return fail(net, SNN_EOVERFLOW, "spike records dropped (buffer or cap too small)");
   return SNN_OK;
 }
@@ -447,25 +508,22 @@ int snn_set_record_capacity(snn_net* net, int64_t capacity) {
   if (!net || capacity < 1) return fail(net, SNN_EINVAL, "bad argument");
   int rc = sync(net);
   if (rc) return rc;
+  const long long region = (capacity + net->update_grid - 1) / net->update_grid;
   unsigned long long* nr = nullptr;
-  cudaError_t e = cudaMalloc(&nr, (size_t)capacity * 8);
+  cudaError_t e = cudaMalloc(&nr, (size_t)region * net->update_grid * 8);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_fail(net, e, "cudaMalloc record buffer");
   }
   cudaFree(net->rec);
-  net->device_bytes += ((size_t)capacity - (size_t)net->rec_cap) * 8;
+  net->device_bytes -= (size_t)net->rec_region * net->update_grid * 8;
+  net->device_bytes += (size_t)region * net->update_grid * 8;
   net->rec = nr;
   net->rec_cap = capacity;
+  net->rec_region = region;
   fill_step_params(net);
   free_graphs(net);
-  const unsigned long long zero = 0ull;
-  const unsigned zero32 = 0u;
-  SNN_CUDA(net, cudaMemcpyAsync((char*)net->ctl + offsetof(Ctl, rec_count), &zero, 8,
-                                cudaMemcpyHostToDevice, net->stream));
-  SNN_CUDA(net, cudaMemcpyAsync((char*)net->ctl + offsetof(Ctl, rec_overflow), &zero32, 4,
-                                cudaMemcpyHostToDevice, net->stream));
-  return sync(net);
+  return reset_records(net);
 }
 
 int snn_read_rates(snn_net* net, float* hz, int64_t n, float* pop_hz) {
@@ -504,14 +562,19 @@ int snn_stats(snn_net* net, double* recurrent_events, double* external_events, i
   cudaError_t e;
   Ctl c = read_ctl(net, &e);
   if (e != cudaSuccess) return cuda_fail(net, e, "read control block");
-  std::vector<unsigned long long> part((size_t)net->update_grid);
-  SNN_CUDA(net, cudaMemcpyAsync(part.data(), net->ext_part, part.size() * 8, cudaMemcpyDeviceToHost,
+  std::vector<unsigned long long> ext((size_t)net->update_grid), spk((size_t)net->update_grid);
+  SNN_CUDA(net, cudaMemcpyAsync(ext.data(), net->ext_part, ext.size() * 8, cudaMemcpyDeviceToHost,
+                                net->stream));
+  SNN_CUDA(net, cudaMemcpyAsync(spk.data(), net->spk_part, spk.size() * 8, cudaMemcpyDeviceToHost,
                                 net->stream));
   SNN_CUDA(net, cudaStreamSynchronize(net->stream));
-  unsigned long long ext = 0ull;
-  for (unsigned long long v : part) ext += v;
-  if (recurrent_events) *recurrent_events = (double)c.spikes * (double)net->K;
-  if (external_events) *external_events = (double)ext;
+  unsigned long long se = 0ull, ss = 0ull;
+  for (size_t b = 0; b < ext.size(); ++b) {
+    se += ext[b];
+    ss += spk[b];
+  }
+  if (recurrent_events) *recurrent_events = (double)ss * (double)net->K;
+  if (external_events) *external_events = (double)se;
   if (steps) *steps = (int64_t)c.t;
   return SNN_OK;
 }

@@ -16,13 +16,15 @@
 //   V, C   float[Npad] membrane potential (mV) and calcium.
 //   R      u8[Npad] remaining refractory steps.
 //   acc    int32[Npad] recurrent input of the next step, 2^-16 mV units.
-//   ids    u32[d_max][N] spike lists of the last d_max steps (slot t % d_max);
-//          column c's spikes of a step occupy [c * n_per_col, + cnt[slot][c]).
-//   cnt    u32[d_max][ncol] spikes per column of each slot's step.
-//   ctl    control block (step counter, record counter, totals).
-//   rec    u64 spike records (step << 32 | id), drained by snn_read_spikes.
+//   ids    u32[d_max + 1][N] spike lists of the last d_max + 1 steps (slot
+//          t % (d_max + 1)), cnt[slot] entries each, in neuron-block order.
+//   cnt    u32[d_max + 1] spikes of each slot's step.
+//   ctl    control block (step counter, completion counter, overflow flag).
+//   rec    u64 spike records (step << 32 | id), one region per update block,
+//          rcnt[b] records in region b since the last drain.
 //   colcnt u64[ncol][2] spike counts per column and population.
-//   ext_part u64[update grid] external-event counts summed by each update block.
+//   ext_part, spk_part  u64[update grid] external events and spikes counted
+//          by each update block.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -66,18 +68,19 @@ int make_host_tables(const snn_neuron_params& np, const snn_synapse_params& sp,
 
 // Device control block.
 struct Ctl {
-  long long t;                          // step index of the next update
-  unsigned long long rec_count;         // records appended since the last drain
-  unsigned int rec_overflow;            // set when a record did not fit
-  unsigned int done;                    // delivery blocks finished this step
-  unsigned long long spikes;            // spikes since build
+  long long t;                  // step index of the next update
+  unsigned int unused;
+  unsigned int done;            // delivery blocks finished this step
+  unsigned int rec_overflow;    // set when a record did not fit its region
+  unsigned int pad;
 };
 
 // Everything a step kernel needs, passed by value (constant bank).
 struct StepParams {
   long long N;
   int npc, nexc, W, H, K, dmin, ndel, nslot, rowcap;
-  int ncol, split;  // columns; delivery blocks per source column
+  int ncol;
+  int agg;  // per-warp shared windows for the local half of the synapses
   uint32_t seed_lo, seed_hi;
   float theta, vr, dc, pvv, pcc, pvc_e, pvc_i;
   int32_t jx;
@@ -95,9 +98,11 @@ struct StepParams {
   const void* syn;
   Ctl* ctl;
   unsigned long long* rec;
-  long long rec_cap;
+  long long rec_region;          // records per update block
+  unsigned long long* rcnt;      // records written per region since the last drain
   unsigned long long* colcnt;
   unsigned long long* ext_part;  // external-event partial sums, one per update block
+  unsigned long long* spk_part;  // spike partial sums, one per update block
 };
 
 struct BuildParams {
@@ -117,7 +122,9 @@ cudaError_t launch_build(const BuildParams& bp, int precision, int num_sms,
 cudaError_t launch_init_state(const StepParams& p, cudaStream_t st);
 cudaError_t launch_update(const StepParams& p, int grid, cudaStream_t st);
 int update_grid(long long N, int num_sms);
-cudaError_t launch_deliver(const StepParams& p, int precision, cudaStream_t st);
-int deliver_split(long long ncol, int num_sms);
+cudaError_t launch_deliver(const StepParams& p, int precision, int grid, cudaStream_t st);
+int deliver_grid(int precision, int num_sms, int npc, bool agg);
+cudaError_t launch_sum_parts(const unsigned long long* part, int n, unsigned long long* out,
+                             cudaStream_t st);
 
 }  // namespace snn

@@ -5,23 +5,29 @@
 //   neurons and one Philox4x32-10 block (counter (i/4, t, EXT, 0)) whose 4
 //   words give their external Poisson counts.  It reads and clears their
 //   recurrent input, applies refractoriness, threshold, reset and the exact
-//   propagator with explicitly rounded FP32 operations.  Spikes are ranked per
-//   (tile, column) in shared memory and appended to the per-column spike list
-//   of the step with one global atomic per column and tile; the spike records
-//   are buffered per block and appended with one atomic per flush.
+//   propagator with explicitly rounded FP32 operations.  A block buffers the
+//   spikes of a few consecutive tiles in shared memory and appends them to the
+//   step's spike list with one atomic per flush, so neighbouring list entries
+//   come from neighbouring neurons.  Spike records go to a region of the
+//   record buffer owned by the block; spike and external-event totals to
+//   per-block partial sums.
 //
 // deliver_kernel (event-driven delivery, Sec. 1), "pull by delay": the input
 //   of step t+1 is the sum over delays d of bucket d of every neuron that
 //   spiked at step t+1-d, so only one N-entry accumulator (resident in L2)
-//   receives additions, not a d_max-slot ring.  One block owns one source
-//   column: it walks the (delay bucket, spiker) items of that column over the
-//   last d_max steps in batches of 32 per warp, streams the concatenated
-//   buckets in 16-byte chunks, adds the local half of the synapses (targets in
-//   the same column) into a shared-memory copy of the column's accumulator,
-//   and sends the remote half to L2 as fire-and-forget int32 reductions.  The
-//   shared accumulator is flushed with coalesced reductions at the end.
-//   Integer addition makes the result independent of the order.  The last
-//   block to finish advances the step counter.
+//   receives additions, not a d_max-slot ring.  The (delay bucket, spiker)
+//   items of the last d_max steps form one virtual list, split evenly over a
+//   persistent grid.  A warp takes 32 consecutive items: lane e resolves item
+//   e, then the warp streams the concatenated buckets in 16-byte chunks (4
+//   synapses per lane, two chunks in flight).  The item a chunk belongs to is
+//   found from a ballot over the items' start offsets and the item's fields
+//   travel by shuffle, so the inner loop reads no shared memory.  Each
+//   synapse's weight goes to L2 as a fire-and-forget int32 reduction, except
+//   when all 32 items come from one column and carry enough synapses: then the
+//   local half (targets in that column) is summed in a per-warp shared-memory
+//   window first and flushed with coalesced reductions.  Integer addition
+//   makes the result independent of the order.  The last block to finish
+//   advances the step counter.
 #include "snn_device.cuh"
 #include "snn_internal.h"
 
@@ -31,7 +37,7 @@ namespace {
 constexpr int kUpdateThreads = 256;
 constexpr int kDeliverThreads = 256;
 constexpr int kTile = kUpdateThreads * 4;    // neurons per update tile
-constexpr int kRecBuf = 3 * kTile;           // block-local spike-record buffer
+constexpr int kSpikeBuf = 3 * kTile;         // block-local spike buffer
 constexpr int kTileCols = kTile / 2 + 2;     // columns a tile can touch (npc >= 2)
 
 struct NeuronOut {
@@ -82,52 +88,59 @@ __device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
                : "memory");
 }
 
-// Append the block's buffered records (step << 32 | id).
-__device__ __forceinline__ void flush_records(const StepParams& P, long long t, uint32_t* s_rec,
-                                              unsigned* s_fill, unsigned long long* s_rbase) {
+// Append the block's buffered spikes to the step's list (one atomic) and to
+// the block's own region of the record buffer (step << 32 | id).
+__device__ __forceinline__ void flush_spikes(const StepParams& P, long long t, int slot,
+                                             uint32_t* s_buf, unsigned* s_fill,
+                                             unsigned* s_base, unsigned long long* s_rc,
+                                             unsigned long long* s_spk) {
   const unsigned n = *s_fill;  // block-uniform (read after a barrier)
   if (n == 0u) return;
-  if (threadIdx.x == 0) {
-    *s_rbase = atomicAdd(&P.ctl->rec_count, (unsigned long long)n);
-    atomicAdd(&P.ctl->spikes, (unsigned long long)n);
-  }
+  if (threadIdx.x == 0) *s_base = atomicAdd(P.cnt + slot, n);
   __syncthreads();
-  const unsigned long long rbase = *s_rbase;
+  const unsigned base = *s_base;
+  const unsigned long long rc = *s_rc;
+  uint32_t* list = P.ids + (long long)slot * P.N + base;
+  unsigned long long* region = P.rec + (long long)blockIdx.x * P.rec_region;
   for (unsigned e = threadIdx.x; e < n; e += blockDim.x) {
-    const unsigned long long ri = rbase + e;
-    if ((long long)ri < P.rec_cap)
-      P.rec[ri] = ((unsigned long long)(unsigned)t << 32) | s_rec[e];
-    else
-      P.ctl->rec_overflow = 1u;
+    const uint32_t id = s_buf[e];
+    list[e] = id;
+    const unsigned long long ri = rc + e;
+    if ((long long)ri < P.rec_region) region[ri] = ((unsigned long long)(unsigned)t << 32) | id;
   }
   __syncthreads();
-  if (threadIdx.x == 0) *s_fill = 0u;
+  if (threadIdx.x == 0) {
+    if ((long long)(rc + n) > P.rec_region) P.ctl->rec_overflow = 1u;
+    *s_rc = rc + n;
+    *s_spk += n;
+    *s_fill = 0u;
+  }
   __syncthreads();
 }
 
 // Grid-stride over tiles; the grid size is fixed per net, so block b owns
-// ext_part[b].
+// ext_part[b], spk_part[b] and record region b.
 __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams P) {
-  __shared__ uint32_t s_rec[kRecBuf];
+  __shared__ uint32_t s_buf[kSpikeBuf];
   __shared__ uint32_t s_thr[kMaxPoisThr + 1];
   __shared__ uint8_t s_guide[256];
-  __shared__ unsigned s_tcnt[kTileCols];     // spikes per column of the tile
-  __shared__ unsigned s_tbase[kTileCols];    // their offsets in the column lists
-  __shared__ unsigned s_tpop[kTileCols][2];  // E / I spikes per column
-  __shared__ unsigned s_fill;
-  __shared__ unsigned long long s_rbase;
+  __shared__ unsigned s_tpop[kTileCols][2];  // E / I spikes per column of the tile
+  __shared__ unsigned s_fill, s_base;
+  __shared__ unsigned long long s_rc, s_spk;
   __shared__ unsigned s_ksum[kUpdateThreads / 32];
 
   const long long t = P.ctl->t;
   const int slot = (int)(t % P.nslot);
   for (int m = threadIdx.x; m < 256; m += blockDim.x) s_guide[m] = P.pois_guide[m];
   for (int m = threadIdx.x; m <= kMaxPoisThr; m += blockDim.x) s_thr[m] = P.pois_thr[m];
-  if (threadIdx.x == 0) s_fill = 0u;
+  if (threadIdx.x == 0) {
+    s_fill = 0u;
+    s_rc = P.rcnt[blockIdx.x];
+    s_spk = 0ull;
+  }
   unsigned ksum = 0u;
   const long long quads = (P.N + 3) / 4;
   const long long tiles = (quads + kUpdateThreads - 1) / kUpdateThreads;
-  unsigned* cnt = P.cnt + (long long)slot * P.ncol;
-  uint32_t* ids = P.ids + (long long)slot * P.N;
 
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long first = tile * kTile;
@@ -135,7 +148,6 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
     const int col0 = (int)(first / P.npc);
     const int ncols = (int)(last / P.npc) - col0 + 1;
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
-      s_tcnt[k] = 0u;
       s_tpop[k][0] = 0u;
       s_tpop[k][1] = 0u;
     }
@@ -143,9 +155,6 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
 
     const long long q = tile * kUpdateThreads + threadIdx.x;
     const long long i0 = q * 4;
-    unsigned spk_rank[4] = {0u, 0u, 0u, 0u};
-    int spk_col[4] = {0, 0, 0, 0};
-    bool spk[4] = {false, false, false, false};
     if (i0 < P.N) {
       const uint4 x = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)t, kTagExt, 0u), P.seed_lo, P.seed_hi);
       const float4 v4 = reinterpret_cast<const float4*>(P.V)[q];
@@ -171,14 +180,11 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
         vout[e] = o.v;
         cout[e] = o.c;
         rout[e] = o.r;
-        spk_col[e] = col;
         if (i0 + e < P.N) {
           ksum += (unsigned)k;
           if (o.spike) {
-            spk[e] = true;
-            spk_rank[e] = atomicAdd(&s_tcnt[col - col0], 1u);
+            s_buf[atomicAdd(&s_fill, 1u)] = (uint32_t)(i0 + e);
             atomicAdd(&s_tpop[col - col0][exc ? 0 : 1], 1u);
-            s_rec[atomicAdd(&s_fill, 1u)] = (uint32_t)(i0 + e);
           }
         }
         if (++l == P.npc) {
@@ -192,25 +198,15 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
                                                       (unsigned char)rout[2], (unsigned char)rout[3]);
     }
     __syncthreads();
-    // one reservation per column of the tile in that column's spike list
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
-      const unsigned n = s_tcnt[k];
-      if (n) {
-        s_tbase[k] = atomicAdd(&cnt[col0 + k], n);
-        if (s_tpop[k][0]) atomicAdd(&P.colcnt[2 * (col0 + k)], (unsigned long long)s_tpop[k][0]);
-        if (s_tpop[k][1]) atomicAdd(&P.colcnt[2 * (col0 + k) + 1], (unsigned long long)s_tpop[k][1]);
-      }
+      if (s_tpop[k][0]) atomicAdd(&P.colcnt[2 * (col0 + k)], (unsigned long long)s_tpop[k][0]);
+      if (s_tpop[k][1]) atomicAdd(&P.colcnt[2 * (col0 + k) + 1], (unsigned long long)s_tpop[k][1]);
     }
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-      if (spk[e])
-        ids[(long long)spk_col[e] * P.npc + s_tbase[spk_col[e] - col0] + spk_rank[e]] =
-            (uint32_t)(i0 + e);
-    if (s_fill > (unsigned)(kRecBuf - kTile)) flush_records(P, t, s_rec, &s_fill, &s_rbase);
+    if (s_fill > (unsigned)(kSpikeBuf - kTile))
+      flush_spikes(P, t, slot, s_buf, &s_fill, &s_base, &s_rc, &s_spk);
   }
   __syncthreads();
-  flush_records(P, t, s_rec, &s_fill, &s_rbase);
+  flush_spikes(P, t, slot, s_buf, &s_fill, &s_base, &s_rc, &s_spk);
 
   // external events: per-block partial sum, no atomics
 #pragma unroll
@@ -221,6 +217,8 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
     unsigned long long tot = 0ull;
     for (int w = 0; w < kUpdateThreads / 32; ++w) tot += s_ksum[w];
     P.ext_part[blockIdx.x] += tot;
+    P.spk_part[blockIdx.x] += s_spk;
+    P.rcnt[blockIdx.x] = s_rc;
   }
 }
 
@@ -235,16 +233,13 @@ __device__ __forceinline__ int wrap_near(int v, int n) {
   return wrap(v, n);
 }
 
-// Per-warp staging of one batch of 32 delivery items.
-struct WarpBatch {
-  int pre[33];         // exclusive prefix of the items' slot counts
-  long long base[32];  // table slot of the item's first synapse, minus pre[e]
-  float wscale[32];    // +-2^16: fixed-point scale with the source's sign
-};
+constexpr int kDeliverWarps = kDeliverThreads / 32;
 
+// Deliver one synapse record.  win != nullptr: targets in the item's own
+// column go to the warp's shared window instead of L2.
 template <int PREC>
 __device__ __forceinline__ void deliver_record(uint32_t code, uint32_t wbits, float wscale,
-                                               int cx, int cy, int32_t* s_acc,
+                                               uint32_t colxy, int32_t* win,
                                                const StepParams& P) {
   if (code == kPad) return;
   float w;
@@ -255,110 +250,97 @@ __device__ __forceinline__ void deliver_record(uint32_t code, uint32_t wbits, fl
   const int32_t wfx = __float2int_rn(w);
   const int l = (int)(code & 0x7FFu);
   const uint32_t off = (code >> 11) & 63u;
-  if (off == (uint32_t)kCenterCode) {
-    atomicAdd(s_acc + l, wfx);
+  if (win != nullptr && off == (uint32_t)kCenterCode) {
+    atomicAdd(win + l, wfx);
   } else {
+    const int cx = (int)(colxy & 0xFFFFu), cy = (int)(colxy >> 16);
     const int ty = wrap_near(cy + (int)(off >> 3) - 3, P.H);
     const int tx = wrap_near(cx + (int)(off & 7u) - 3, P.W);
     red_add(P.acc + (ty * P.W + tx) * P.npc + l, wfx);
   }
 }
 
+// One warp, one batch of up to 32 consecutive items.
 template <int PREC>
-__global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepParams P) {
-  constexpr int kWarps = kDeliverThreads / 32;
-  __shared__ int32_t s_acc[2048];
-  __shared__ unsigned s_pref[kMaxDelays + 1];
-  __shared__ long long s_list[kMaxDelays];
-  __shared__ unsigned s_next;
-  __shared__ WarpBatch s_wb[kWarps];
-
-  const long long t = P.ctl->t;
-  const int c = (int)(blockIdx.x / (unsigned)P.split);
-  const int part = (int)(blockIdx.x - (unsigned)c * (unsigned)P.split);
-  const int cy = c / P.W;
-  const int cx = c - cy * P.W;
-  for (int l = threadIdx.x; l < P.npc; l += blockDim.x) s_acc[l] = 0;
-  if (threadIdx.x < 32) {
-    const int b = threadIdx.x;
-    unsigned n = 0u;
-    long long off = 0;
-    if (b < P.ndel) {
-      const long long s = t + 1 - (P.dmin + b);
-      if (s >= 0) {
-        const int slot = (int)(s % P.nslot);
-        n = P.cnt[(long long)slot * P.ncol + c];
-        off = (long long)slot * P.N + (long long)c * P.npc;
-      }
-    }
-    unsigned incl = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (b >= o) incl += v;
-    }
-    s_pref[b + 1] = incl;
-    if (b == 0) {
-      s_pref[0] = 0u;
-      s_next = 0u;
-    }
-    s_list[b] = off;
-  }
-  __syncthreads();
-
-  const unsigned total = s_pref[P.ndel];
-  const unsigned lo = (unsigned)(((unsigned long long)total * part) / P.split);
-  const unsigned hi = (unsigned)(((unsigned long long)total * (part + 1)) / P.split);
+__device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item, unsigned hi,
+                                              const unsigned* s_pref, const long long* s_list,
+                                              int32_t* win) {
   const int lane = threadIdx.x & 31;
-  WarpBatch& wb = s_wb[threadIdx.x >> 5];
+  int len = 0;
+  unsigned long long base = 0ull;
+  float ws = 0.f;
+  uint32_t colxy = 0u;
+  int col = -1;
+  if (item < hi) {
+    int b = 0;
+    while (item >= s_pref[b + 1]) ++b;
+    const uint32_t j = P.ids[s_list[b] + (item - s_pref[b])];
+    const uint8_t* be = P.bend + (long long)j * kBendStride;
+    const int beg = (b ? (int)be[b - 1] : 0) * kSlotUnit;
+    const int end = (int)be[b] * kSlotUnit;
+    len = end - beg;
+    base = (unsigned long long)j * (unsigned long long)P.rowcap + (unsigned long long)beg;
+    col = (int)(j / (uint32_t)P.npc);
+    ws = (int)(j - (uint32_t)col * (uint32_t)P.npc) < P.nexc ? 65536.0f : -65536.0f;
+    const int cy = col / P.W;
+    colxy = ((uint32_t)cy << 16) | (uint32_t)(col - cy * P.W);
+  }
+  // compact the non-empty items to lanes 0..nit-1
+  const unsigned cm = __ballot_sync(0xFFFFFFFFu, len > 0);
+  const int nit = __popc(cm);
+  const int src = lane < nit ? (int)__fns(cm, 0u, lane + 1) : 0;
+  int lenc = __shfl_sync(0xFFFFFFFFu, len, src);
+  const unsigned blo0 = __shfl_sync(0xFFFFFFFFu, (unsigned)base, src);
+  const unsigned bhi0 = __shfl_sync(0xFFFFFFFFu, (unsigned)(base >> 32), src);
+  const float wsc = __shfl_sync(0xFFFFFFFFu, ws, src);
+  const uint32_t cxy = __shfl_sync(0xFFFFFFFFu, colxy, src);
+  const int colc = __shfl_sync(0xFFFFFFFFu, col, src);
+  if (lane >= nit) lenc = 0;
+  int incl = lenc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int pre = incl - lenc;  // first flat slot of compact item `lane`
+  const int T = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  const unsigned long long bc = (((unsigned long long)bhi0 << 32) | blo0) - (unsigned long long)pre;
+  const unsigned blo = (unsigned)bc, bhi = (unsigned)(bc >> 32);
+  const bool mine = lane < nit;
+  const unsigned le_mask = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+  // one source column and enough synapses: sum the local half in the window
+  const int col0 = __shfl_sync(0xFFFFFFFFu, colc, 0);
+  const bool agg = win != nullptr && T >= 2 * P.npc &&
+                   __all_sync(0xFFFFFFFFu, !mine || colc == col0);
+  int32_t* w = agg ? win : nullptr;
 
-  while (true) {
-    unsigned k0 = 0u;
-    if (lane == 0) k0 = atomicAdd(&s_next, 32u);
-    k0 = __shfl_sync(0xFFFFFFFFu, k0, 0);
-    if (lo + k0 >= hi) break;
-    // phase A: lane e resolves item e of the batch
-    const unsigned item = lo + k0 + lane;
-    int len = 0;
-    if (item < hi) {
-      int b = 0;
-      while (item >= s_pref[b + 1]) ++b;
-      const uint32_t j = P.ids[s_list[b] + (item - s_pref[b])];
-      const uint8_t* be = P.bend + (long long)j * kBendStride;
-      const int beg = (b ? (int)be[b - 1] : 0) * kSlotUnit;
-      const int end = (int)be[b] * kSlotUnit;
-      len = end - beg;
-      wb.base[lane] = (long long)j * P.rowcap + beg;
-      wb.wscale[lane] = (int)(j - (uint32_t)c * (uint32_t)P.npc) < P.nexc ? 65536.0f : -65536.0f;
-    }
-    int incl = len;
+  for (int f0 = 0; f0 < T; f0 += 256) {
+    uint32_t code[2][4], wbits[2][4];
+    float wsl[2];
+    uint32_t cxl[2];
+    bool in[2];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    wb.pre[lane + 1] = incl;
-    if (lane == 0) wb.pre[0] = 0;
-    if (item < hi) wb.base[lane] -= incl - len;
-    __syncwarp();
-    const int T = wb.pre[32];
-
-    // phase B: stream the concatenated buckets, 4 slots per lane per chunk,
-    // two chunks in flight
-    for (int f0 = 0; f0 < T; f0 += 256) {
-      int e[2];
-      uint32_t code[2][4], wbits[2][4];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int f = f0 + u * 128 + lane * 4;
-        e[u] = -1;
-        if (f < T) {
-          int x = 0;
-#pragma unroll
-          for (int st = 16; st >= 1; st >>= 1)
-            if (wb.pre[x + st] <= f) x += st;
-          e[u] = x;
-          const long long slot = wb.base[x] + f;
+    for (int u = 0; u < 2; ++u) {
+      const int fu = f0 + u * 128;
+      in[u] = false;
+      wsl[u] = 0.f;
+      cxl[u] = 0u;
+      if (fu < T) {
+        // item of the chunk at flat slot fu + 4 * lane: the item holding fu,
+        // plus the items that start between fu and the lane's chunk
+        const int ebase = __popc(__ballot_sync(0xFFFFFFFFu, mine && pre <= fu)) - 1;
+        const int pos = (pre - fu) >> 2;
+        const unsigned bit = (mine && pre > fu && pos < 32) ? (1u << pos) : 0u;
+        const unsigned starts = __reduce_or_sync(0xFFFFFFFFu, bit);
+        const int e = ebase + __popc(starts & le_mask);
+        const unsigned bl = __shfl_sync(0xFFFFFFFFu, blo, e);
+        const unsigned bh = __shfl_sync(0xFFFFFFFFu, bhi, e);
+        wsl[u] = __shfl_sync(0xFFFFFFFFu, wsc, e);
+        cxl[u] = __shfl_sync(0xFFFFFFFFu, cxy, e);
+        const int f = fu + 4 * lane;
+        in[u] = f < T;
+        if (in[u]) {
+          const long long slot = (long long)(((unsigned long long)bh << 32) | bl) + f;
           if (PREC == SNN_EXACT_F16W) {
             const uint4 r = __ldcs(reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(P.syn) + slot));
             const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
@@ -378,29 +360,83 @@ __global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepPara
           }
         }
       }
+    }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        if (e[u] >= 0) {
-          const float ws = wb.wscale[e[u]];
+    for (int u = 0; u < 2; ++u) {
+      if (in[u]) {
 #pragma unroll
-          for (int qd = 0; qd < 4; ++qd)
-            deliver_record<PREC>(code[u][qd], wbits[u][qd], ws, cx, cy, s_acc, P);
-        }
+        for (int qd = 0; qd < 4; ++qd)
+          deliver_record<PREC>(code[u][qd], wbits[u][qd], wsl[u], cxl[u], w, P);
+      }
+    }
+  }
+  if (agg) {
+    // flush the window with coalesced reductions, leaving it zeroed
+    __syncwarp();
+    int32_t* dst = P.acc + (long long)col0 * P.npc;
+    for (int l = lane; l < P.npc; l += 32) {
+      const int32_t v = win[l];
+      if (v) {
+        red_add(dst + l, v);
+        win[l] = 0;
       }
     }
     __syncwarp();
   }
+}
 
-  // flush the column's shared accumulator with coalesced reductions
-  __syncthreads();
-  int32_t* dst = P.acc + (long long)c * P.npc;
-  for (int l = threadIdx.x; l < P.npc; l += blockDim.x) {
-    const int32_t v = s_acc[l];
-    if (v) red_add(dst + l, v);
+template <int PREC>
+__global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepParams P) {
+  extern __shared__ int32_t s_win[];  // [warps][n_per_col] when P.agg
+  __shared__ unsigned s_pref[kMaxDelays + 1];
+  __shared__ long long s_list[kMaxDelays];
+  __shared__ unsigned s_next;
+
+  const long long t = P.ctl->t;
+  // the slot that the next update fills holds step t - d_max: no longer read
+  if (blockIdx.x == 0 && threadIdx.x == 0) P.cnt[(t + 1) % P.nslot] = 0u;
+  const int lane = threadIdx.x & 31;
+  int32_t* win = P.agg ? s_win + (threadIdx.x >> 5) * P.npc : nullptr;
+  if (win)
+    for (int l = lane; l < P.npc; l += 32) win[l] = 0;
+  if (threadIdx.x < 32) {
+    const int b = threadIdx.x;
+    unsigned n = 0u;
+    long long off = 0;
+    if (b < P.ndel) {
+      const long long s = t + 1 - (P.dmin + b);
+      if (s >= 0) {
+        const long long slot = s % P.nslot;
+        n = P.cnt[slot];
+        off = slot * P.N;
+      }
+    }
+    unsigned incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (b >= o) incl += v;
+    }
+    s_pref[b + 1] = incl;
+    if (b == 0) {
+      s_pref[0] = 0u;
+      s_next = 0u;
+    }
+    s_list[b] = off;
   }
-  // this column's count of the slot that the next update overwrites
-  const int next_slot = (int)((t + 1) % P.nslot);
-  if (P.split == 1 && threadIdx.x == 0) P.cnt[(long long)next_slot * P.ncol + c] = 0u;
+  __syncthreads();
+
+  // this block's contiguous share of the step's items, 32 per warp batch
+  const unsigned total = s_pref[P.ndel];
+  const unsigned lo = (unsigned)(((unsigned long long)total * blockIdx.x) / gridDim.x);
+  const unsigned hi = (unsigned)(((unsigned long long)total * (blockIdx.x + 1)) / gridDim.x);
+  while (true) {
+    unsigned k0 = 0u;
+    if (lane == 0) k0 = atomicAdd(&s_next, 32u);
+    k0 = __shfl_sync(0xFFFFFFFFu, k0, 0);
+    if (lo + k0 >= hi) break;
+    deliver_batch<PREC>(P, lo + k0 + lane, hi, s_pref, s_list, win);
+  }
 
   // the last block to finish closes the step
   __syncthreads();
@@ -409,12 +445,19 @@ __global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepPara
     const unsigned prev = atomicAdd(&P.ctl->done, 1u);
     if (prev == gridDim.x - 1) {
       __threadfence();
-      if (P.split > 1)
-        for (int k = 0; k < P.ncol; ++k) P.cnt[(long long)next_slot * P.ncol + k] = 0u;
       P.ctl->done = 0u;
       P.ctl->t = t + 1;
     }
   }
+}
+
+// Sum of the per-block spike counts (measurement helper).
+__global__ void sum_parts_kernel(const unsigned long long* part, int n, unsigned long long* out) {
+  unsigned long long s = 0ull;
+  for (int i = threadIdx.x; i < n; i += 32) s += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  if (threadIdx.x == 0) *out = s;
 }
 
 }  // namespace
@@ -433,21 +476,41 @@ cudaError_t launch_update(const StepParams& p, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Blocks per source column: enough blocks for 4 per SM on small grids.
-int deliver_split(long long ncol, int num_sms) {
-  const long long target = 4LL * num_sms;
-  long long s = (target + ncol - 1) / ncol;
-  if (s < 1) s = 1;
-  if (s > 64) s = 64;
-  return (int)s;
+size_t deliver_smem(int npc, bool agg) {
+  return agg ? (size_t)kDeliverWarps * (size_t)npc * sizeof(int32_t) : 0u;
 }
 
-cudaError_t launch_deliver(const StepParams& p, int precision, cudaStream_t st) {
-  const unsigned grid = (unsigned)(p.ncol * p.split);
+// Delivery grid: a persistent grid at full occupancy.
+int deliver_grid(int precision, int num_sms, int npc, bool agg) {
+  const size_t smem = deliver_smem(npc, agg);
+  int per_sm = 0;
+  if (precision == SNN_EXACT_F16W) {
+    cudaFuncSetAttribute(deliver_kernel<SNN_EXACT_F16W>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, deliver_kernel<SNN_EXACT_F16W>,
+                                                  kDeliverThreads, smem);
+  } else {
+    cudaFuncSetAttribute(deliver_kernel<SNN_EXACT_F32W>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, deliver_kernel<SNN_EXACT_F32W>,
+                                                  kDeliverThreads, smem);
+  }
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * num_sms;
+}
+
+cudaError_t launch_deliver(const StepParams& p, int precision, int grid, cudaStream_t st) {
+  const size_t smem = deliver_smem(p.npc, p.agg != 0);
   if (precision == SNN_EXACT_F16W)
-    deliver_kernel<SNN_EXACT_F16W><<<grid, kDeliverThreads, 0, st>>>(p);
+    deliver_kernel<SNN_EXACT_F16W><<<grid, kDeliverThreads, smem, st>>>(p);
   else
-    deliver_kernel<SNN_EXACT_F32W><<<grid, kDeliverThreads, 0, st>>>(p);
+    deliver_kernel<SNN_EXACT_F32W><<<grid, kDeliverThreads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_parts(const unsigned long long* part, int n, unsigned long long* out,
+                             cudaStream_t st) {
+  sum_parts_kernel<<<1, 32, 0, st>>>(part, n, out);
   return cudaGetLastError();
 }
 
