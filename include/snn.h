@@ -175,6 +175,47 @@ int snn_info(snn_net* net, int64_t* info, int n);
  */
 int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes);
 
+/*
+ * snn_update_noalloc -- one neuron-update step on buffers the caller owns,
+ * allocating nothing.  The paper has no counterpart: this entry point exists
+ * for callers that cannot let a library call cudaMalloc -- a loop being
+ * recorded into a CUDA graph (allocation is not allowed during stream
+ * capture), a process whose device memory is already reserved by another
+ * framework's allocator or a fixed arena, or a real-time loop that cannot
+ * afford an allocation's implicit synchronisation.
+ *
+ * It runs the same update kernel as snn_step for step `step` of a
+ * grid_w x grid_h network of N = grid_w * grid_h * n_per_col neurons (the
+ * external Poisson input is keyed on (seed, neuron, step), so the result
+ * equals snn_step's update of that step given the same state and input).
+ * Device buffers, each of at least ceil(N / 4) * 4 elements (the kernel reads
+ * and writes whole groups of 4 neurons):
+ *   v, c          float, 16-byte aligned: membrane potential and calcium, in/out;
+ *   refractory    u8, 4-byte aligned: remaining refractory steps, in/out;
+ *   input         int32, 16-byte aligned: recurrent input of this step in
+ *                 2^-16 mV units, read and then cleared to zero;
+ *   spikes        u32[N]: receives the indices of the neurons that fired;
+ *   col_counts    u64[2 * columns] or NULL: spikes per column (E, I).
+ * Host outputs: *n_spikes (entries written to spikes), *ext_events (sum of
+ * the external Poisson counts; may be NULL).  Synchronises cuda_stream
+ * (a cudaStream_t; NULL is the legacy default stream).
+ *
+ * Its scratch is one fixed device array of 311 808 bytes inside the library
+ * (held on every GPU that loads the library until the process exits), which
+ * limits a call to 16 384 columns (SNN_EINVAL beyond).  Every call shares that
+ * array and clears what it needs at its start, so calls whose GPU work
+ * overlaps (on different streams or threads) race and must be serialised by
+ * the caller.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before capturing a
+ * stream.  Returns SNN_EINVAL for bad parameters, sizes or alignment,
+ * SNN_ECUDA for a CUDA error (message in snn_last_error(NULL)).
+ */
+int snn_update_noalloc(int grid_w, int grid_h, const snn_neuron_params* neuron,
+                       uint64_t seed, int64_t step, float* v, float* c,
+                       uint8_t* refractory, int32_t* input, uint32_t* spikes,
+                       int64_t* n_spikes, int64_t* ext_events,
+                       unsigned long long* col_counts, void* cuda_stream);
+
 /* snn_last_error -- message of the last failure on net (thread-local when net
  * is NULL).  Never NULL; valid until the next call on the same net. */
 const char* snn_last_error(const snn_net* net);

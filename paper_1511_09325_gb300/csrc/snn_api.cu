@@ -63,6 +63,33 @@ int fail(snn_net* net, int code, const std::string& msg) {
   return code;
 }
 
+}  // namespace
+
+namespace snn {
+
+int fail_global(int code, const std::string& msg) { return fail(nullptr, code, msg); }
+
+int validate_neuron_params(const snn_neuron_params* n, std::string* why) {
+  auto bad = [&](const char* m) {
+    *why = m;
+    return SNN_EINVAL;
+  };
+  if (!n) return bad("null parameter struct");
+  if (n->n_per_col < 2 || n->n_per_col > 2048) return bad("n_per_col must be in 2..2048");
+  if (n->n_exc < 0 || n->n_exc > n->n_per_col) return bad("n_exc must be in 0..n_per_col");
+  if (!(n->tau_m > 0.f) || !(n->tau_c > 0.f)) return bad("time constants must be positive");
+  if (!(n->t_ref >= 0.f) || n->t_ref > 200.f) return bad("t_ref must be in 0..200 ms");
+  if (!(n->nu_ext_kHz >= 0.f) || n->nu_ext_kHz > 40.f) return bad("nu_ext_kHz must be in 0..40");
+  if (!std::isfinite(n->theta) || !std::isfinite(n->v_reset) || !std::isfinite(n->dc) ||
+      !std::isfinite(n->gc_exc) || !std::isfinite(n->gc_inh) || !std::isfinite(n->j_ext_mV))
+    return bad("non-finite neuron parameter");
+  return SNN_OK;
+}
+
+}  // namespace snn
+
+namespace {
+
 int cuda_fail(snn_net* net, cudaError_t e, const char* what) {
   return fail(net, e == cudaErrorMemoryAllocation ? SNN_ENOMEM : SNN_ECUDA,
               std::string(what) + ": " + cudaGetErrorString(e));
@@ -112,14 +139,8 @@ int validate(int gw, int gh, const snn_neuron_params* n, const snn_synapse_param
   };
   if (!n || !s) return bad("null parameter struct");
   if (gw < 1 || gh < 1) return bad("grid must be at least 1x1");
-  if (n->n_per_col < 2 || n->n_per_col > 2048) return bad("n_per_col must be in 2..2048");
-  if (n->n_exc < 0 || n->n_exc > n->n_per_col) return bad("n_exc must be in 0..n_per_col");
-  if (!(n->tau_m > 0.f) || !(n->tau_c > 0.f)) return bad("time constants must be positive");
-  if (!(n->t_ref >= 0.f) || n->t_ref > 200.f) return bad("t_ref must be in 0..200 ms");
-  if (!(n->nu_ext_kHz >= 0.f) || n->nu_ext_kHz > 40.f) return bad("nu_ext_kHz must be in 0..40");
-  if (!std::isfinite(n->theta) || !std::isfinite(n->v_reset) || !std::isfinite(n->dc) ||
-      !std::isfinite(n->gc_exc) || !std::isfinite(n->gc_inh) || !std::isfinite(n->j_ext_mV))
-    return bad("non-finite neuron parameter");
+  const int nrc = snn::validate_neuron_params(n, why);
+  if (nrc != SNN_OK) return nrc;
   if (s->k_out < 1) return bad("k_out must be positive");
   if (!(s->frac_local >= 0.f && s->frac_local <= 1.f)) return bad("frac_local must be in [0, 1]");
   if (!(s->lambda_cols > 0.f)) return bad("lambda_cols must be positive");

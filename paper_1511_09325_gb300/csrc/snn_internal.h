@@ -65,6 +65,8 @@ struct HostTables {
 
 int make_host_tables(const snn_neuron_params& np, const snn_synapse_params& sp,
                      int precision, HostTables* out, std::string* err);
+// The neuron-update part only: Poisson table, propagators, J_ext, refractory.
+int make_neuron_tables(const snn_neuron_params& np, HostTables* out, std::string* err);
 
 // Device control block.
 struct Ctl {
@@ -115,6 +117,10 @@ struct BuildParams {
   void* syn;
   uint8_t* bend;
 };
+
+// Shared host helpers (snn_api.cu).
+int fail_global(int code, const std::string& msg);
+int validate_neuron_params(const snn_neuron_params* n, std::string* why);
 
 // Kernel launchers (snn_build.cu / snn_step.cu).
 cudaError_t launch_build(const BuildParams& bp, int precision, int num_sms,

@@ -113,9 +113,7 @@ uint32_t half_magnitude_rne(double a) {
 
 }  // namespace
 
-int make_host_tables(const snn_neuron_params& np, const snn_synapse_params& sp,
-                     int precision, HostTables* t, std::string* err) {
-  stencil_table(sp.stencil_radius, (double)sp.lambda_cols, t);
+int make_neuron_tables(const snn_neuron_params& np, HostTables* t, std::string* err) {
   int rc = poisson_table((double)np.nu_ext_kHz * 1.0, t, err);
   if (rc != SNN_OK) return rc;
 
@@ -141,6 +139,14 @@ int make_host_tables(const snn_neuron_params& np, const snn_synapse_params& sp,
   t->pcc = (float)pcc;
   t->jx = (int32_t)std::rint((double)np.j_ext_mV * 65536.0);
   t->nref = (int)std::rint((double)np.t_ref / h);
+  return SNN_OK;
+}
+
+int make_host_tables(const snn_neuron_params& np, const snn_synapse_params& sp,
+                     int precision, HostTables* t, std::string* err) {
+  stencil_table(sp.stencil_radius, (double)sp.lambda_cols, t);
+  int rc = make_neuron_tables(np, t, err);
+  if (rc != SNN_OK) return rc;
   t->k_local = (int)std::rint((double)sp.frac_local * (double)sp.k_out);
 
   // Weights: w = mu (1 + cv Q), clipped to the source population's sign,

@@ -21,8 +21,8 @@ PRECISIONS = {"f32w": SNN_EXACT_F32W, "f16w": SNN_EXACT_F16W}
 # every symbol the header declares
 EXPORTS = ("snn_build", "snn_step", "snn_read_spikes", "snn_pending_spikes",
            "snn_set_record_capacity", "snn_read_rates", "snn_stats", "snn_get_state",
-           "snn_read_synapses", "snn_info", "snn_step_profiled", "snn_last_error",
-           "snn_destroy")
+           "snn_read_synapses", "snn_info", "snn_step_profiled", "snn_update_noalloc",
+           "snn_last_error", "snn_destroy")
 
 
 class SnnError(RuntimeError):
@@ -73,6 +73,8 @@ def load(path=LIB_PATH):
     L.snn_read_synapses.argtypes = [vp, i64, i64, vp, vp, vp]
     L.snn_info.argtypes = [vp, vp, i32]
     L.snn_step_profiled.argtypes = [vp, i64, vp, vp]
+    L.snn_update_noalloc.argtypes = [i32, i32, P(NeuronParams), ctypes.c_uint64, i64,
+                                     vp, vp, vp, vp, vp, P(i64), P(i64), vp, vp]
     L.snn_last_error.argtypes = [vp]
     L.snn_last_error.restype = ctypes.c_char_p
     L.snn_destroy.argtypes = [vp]
@@ -188,6 +190,21 @@ def snn_step_profiled(handle, n_steps):
     by = np.zeros(2, np.float64)
     _check(load().snn_step_profiled(handle, int(n_steps), _p(ms), _p(by)), handle)
     return ms, by
+
+
+def snn_update_noalloc(grid_w, grid_h, neuron, seed, step, v, c, refractory, input_fx,
+                       spikes, col_counts=None, stream=None):
+    """One neuron-update step on caller-owned device buffers (raw pointers).
+
+    No allocation happens inside the library; see include/snn.h for the buffer
+    sizes and alignment.  Returns (n_spikes, ext_events)."""
+    n = neuron_struct(neuron)
+    ns, ne = ctypes.c_int64(), ctypes.c_int64()
+    rc = load().snn_update_noalloc(int(grid_w), int(grid_h), ctypes.byref(n), int(seed), int(step),
+                                   v, c, refractory, input_fx, spikes, ctypes.byref(ns),
+                                   ctypes.byref(ne), col_counts, stream)
+    _check(rc, None)
+    return ns.value, ne.value
 
 
 def snn_destroy(handle):
