@@ -6,9 +6,9 @@
 //   words give their external Poisson counts.  It reads and clears their
 //   recurrent input, applies refractoriness, threshold, reset and the exact
 //   propagator with explicitly rounded FP32 operations.  A block buffers the
-//   spikes of a few consecutive tiles in shared memory and appends them to the
-//   step's spike list with one atomic per flush, so neighbouring list entries
-//   come from neighbouring neurons.  Spike records go to a region of the
+//   spikes of a few tiles in shared memory, grouped by column, and appends them
+//   to the step's spike list with one atomic per flush, so neighbouring list
+//   entries come from the same column.  Spike records go to a region of the
 //   record buffer owned by the block; spike and external-event totals to
 //   per-block partial sums.
 //
@@ -23,7 +23,8 @@
 //   found from a ballot over the items' start offsets and the item's fields
 //   travel by shuffle, so the inner loop reads no shared memory.  Each
 //   synapse's weight goes to L2 as a fire-and-forget int32 reduction, except
-//   when all 32 items come from one column and carry enough synapses: then the
+//   when all items of the batch come from one column and carry at least
+//   n_per_col / 2 synapse slots: then the
 //   local half (targets in that column) is summed in a per-warp shared-memory
 //   window first and flushed with coalesced reductions.  Integer addition
 //   makes the result independent of the order.  The last block to finish
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
   __shared__ uint32_t s_thr[kMaxPoisThr + 1];
   __shared__ uint8_t s_guide[256];
   __shared__ unsigned s_tpop[kTileCols][2];  // E / I spikes per column of the tile
+  __shared__ unsigned s_tpos[kTileCols];     // buffer offset of each column's spikes
   __shared__ unsigned s_fill, s_base;
   __shared__ unsigned long long s_rc, s_spk;
   __shared__ unsigned s_ksum[kUpdateThreads / 32];
@@ -155,6 +157,8 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
 
     const long long q = tile * kUpdateThreads + threadIdx.x;
     const long long i0 = q * 4;
+    unsigned rank[4] = {0u, 0u, 0u, 0u};
+    int scol[4] = {-1, -1, -1, -1};
     if (i0 < P.N) {
       const uint4 x = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)t, kTagExt, 0u), P.seed_lo, P.seed_hi);
       const float4 v4 = reinterpret_cast<const float4*>(P.V)[q];
@@ -183,8 +187,9 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
         if (i0 + e < P.N) {
           ksum += (unsigned)k;
           if (o.spike) {
-            s_buf[atomicAdd(&s_fill, 1u)] = (uint32_t)(i0 + e);
-            atomicAdd(&s_tpop[col - col0][exc ? 0 : 1], 1u);
+            scol[e] = col - col0;
+            rank[e] = atomicAdd(&s_tpop[col - col0][exc ? 0 : 1], 1u);
+            if (!exc) rank[e] |= 0x80000000u;  // ranked among the column's I spikes
           }
         }
         if (++l == P.npc) {
@@ -198,10 +203,31 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
                                                       (unsigned char)rout[2], (unsigned char)rout[3]);
     }
     __syncthreads();
+    // place the tile's spikes in the buffer grouped by column (E then I), so
+    // that neighbouring list entries share a column
+    if (threadIdx.x == 0) {
+      unsigned pos = s_fill;
+      for (int k = 0; k < ncols; ++k) {
+        s_tpos[k] = pos;
+        pos += s_tpop[k][0] + s_tpop[k][1];
+      }
+      s_fill = pos;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (scol[e] >= 0) {
+        const int k = scol[e];
+        const unsigned r = rank[e] & 0x7FFFFFFFu;
+        const unsigned off = (rank[e] & 0x80000000u) ? s_tpop[k][0] + r : r;
+        s_buf[s_tpos[k] + off] = (uint32_t)(i0 + e);
+      }
+    }
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
       if (s_tpop[k][0]) atomicAdd(&P.colcnt[2 * (col0 + k)], (unsigned long long)s_tpop[k][0]);
       if (s_tpop[k][1]) atomicAdd(&P.colcnt[2 * (col0 + k) + 1], (unsigned long long)s_tpop[k][1]);
     }
+    __syncthreads();
     if (s_fill > (unsigned)(kSpikeBuf - kTile))
       flush_spikes(P, t, slot, s_buf, &s_fill, &s_base, &s_rc, &s_spk);
   }
@@ -308,9 +334,10 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
   const unsigned blo = (unsigned)bc, bhi = (unsigned)(bc >> 32);
   const bool mine = lane < nit;
   const unsigned le_mask = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
-  // one source column and enough synapses: sum the local half in the window
+  // one source column and at least n_per_col / 2 synapse slots: sum the
+  // local half in the window (flushing costs one pass over n_per_col entries)
   const int col0 = __shfl_sync(0xFFFFFFFFu, colc, 0);
-  const bool agg = win != nullptr && T >= 2 * P.npc &&
+  const bool agg = win != nullptr && 2 * T >= P.npc &&
                    __all_sync(0xFFFFFFFFu, !mine || colc == col0);
   int32_t* w = agg ? win : nullptr;
 
