@@ -163,6 +163,18 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def reduce_ranks(dist, ms, rec_ev, ext_ev, device):
+    """Whole-job numbers of N replicas: the slowest rank's time, the sum of
+    every rank's events (value = events of all ranks / that time)."""
+    import torch
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ev = torch.tensor([rec_ev, ext_ev], device=device, dtype=torch.float64)
+    dist.all_reduce(ev)
+    return float(t.item()), float(ev[0].item()), float(ev[1].item())
+
+
 def _build_net(snn, torch, cfg, seed, stream):
     n, s = W.neuron_params(), W.synapse_params()
     t0 = time.perf_counter()
@@ -270,12 +282,7 @@ def run_ours(args):
     ms, rec_ev, ext_ev = _timed(net, torch, stream, K, dist.barrier if dist else None)
     clk = clocks.stop()
     if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        ev = torch.tensor([rec_ev, ext_ev], device="cuda", dtype=torch.float64)
-        dist.all_reduce(ev)
-        rec_ev, ext_ev = float(ev[0].item()), float(ev[1].item())
+        ms, rec_ev, ext_ev = reduce_ranks(dist, ms, rec_ev, ext_ev, "cuda")
     info = net.info()
     _, pop_hz = net.rates()
     e2e = _e2e(net, torch, max(1, min(args.e2e_steps, max(K, 1))), ws)
