@@ -62,10 +62,18 @@ def _peaks():
 
 
 def _traffic(workload, kernel):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, if any."""
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or
+    None when there is none or the kernel source changed since it was taken."""
+    import hashlib
+
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             t = json.load(f)
+        src = os.path.join(ROOT, "paper_1511_09325_gb300", "csrc", "snn_step.cu")
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+        if not digest.startswith(t.get("kernel_sha256", "-")):
+            return None
         return t.get(workload, {}).get(kernel)
     except Exception:
         return None
