@@ -37,6 +37,12 @@ struct snn_net {
   long long rec_cap = 0;     // requested total record capacity
   long long rec_region = 0;  // records per update block
   unsigned long long* rcnt = nullptr;
+  unsigned long long* stage = nullptr;   // drained records, contiguous
+  unsigned long long* rpre = nullptr;    // records kept before each region
+  unsigned long long* dhdr = nullptr;    // drain header (device)
+  unsigned long long* hhdr = nullptr;    // drain header (pinned host)
+  unsigned long long* hstage = nullptr;  // drained records (pinned host)
+  long long hstage_cap = 0;
   unsigned long long* colcnt = nullptr;
   unsigned long long* ext_part = nullptr;
   unsigned long long* spk_part = nullptr;
@@ -123,8 +129,10 @@ void free_graphs(snn_net* net) {
 
 void release(snn_net* net) {
   free_graphs(net);
+  if (net->hhdr) cudaFreeHost(net->hhdr);
+  if (net->hstage) cudaFreeHost(net->hstage);
   void* ptrs[] = {net->syn, net->bend, net->V, net->C, net->R, net->acc,
-                  net->ids, net->cnt, net->ctl, net->rec, net->rcnt, net->colcnt,
+                  net->ids, net->cnt, net->ctl, net->rec, net->rcnt, net->stage, net->rpre, net->dhdr, net->colcnt,
                   net->ext_part, net->spk_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -268,6 +276,10 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if ((rc = dalloc(net, &net->ctl, sizeof(Ctl)))) return rc;
   if ((rc = dalloc(net, &net->rec, (size_t)net->rec_region * net->update_grid * 8))) return rc;
   if ((rc = dalloc(net, &net->rcnt, (size_t)net->update_grid * 8))) return rc;
+  if ((rc = dalloc(net, &net->stage, (size_t)net->rec_region * net->update_grid * 8))) return rc;
+  if ((rc = dalloc(net, &net->dhdr, 16))) return rc;
+  if ((rc = dalloc(net, &net->rpre, (size_t)net->update_grid * 8))) return rc;
+  SNN_CUDA(net, cudaMallocHost(&net->hhdr, 16));
   if ((rc = dalloc(net, &net->colcnt, (size_t)net->ncol * 2 * 8))) return rc;
   if ((rc = dalloc(net, &net->ext_part, (size_t)net->update_grid * 8))) return rc;
   if ((rc = dalloc(net, &net->spk_part, (size_t)net->update_grid * 8))) return rc;
@@ -485,42 +497,53 @@ int snn_read_spikes(snn_net* net, int32_t* steps, int32_t* ids, int64_t cap, int
   if (!net || !n_out || cap < 0 || (cap > 0 && (!steps || !ids)))
     return fail(net, SNN_EINVAL, "bad argument");
   *n_out = 0;
-  std::vector<unsigned long long> cnt;
-  long long kept = 0;
-  bool lost = false;
-  int rc = record_counts(net, &cnt, &kept, &lost);
-  if (rc) return rc;
-  if (kept > 0) {
-    // copy the used part of every region (one strided copy), then merge:
-    // each region is in step order, so a sort of (step << 32 | id) puts the
-    // whole window in step order
-    long long width = 0;
-    for (unsigned long long v : cnt) {
-      const long long k = (long long)v < net->rec_region ? (long long)v : net->rec_region;
-      if (k > width) width = k;
+  // compact the regions on the device and reset them, then two copies
+  SNN_CUDA(net, launch_drain_records(net->sp, net->update_grid, net->rpre, net->stage,
+                                     net->dhdr, net->stream));
+  SNN_CUDA(net, cudaMemcpyAsync(net->hhdr, net->dhdr, 16, cudaMemcpyDeviceToHost, net->stream));
+  SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+  const long long kept = (long long)net->hhdr[0];
+  bool lost = net->hhdr[1] != 0ull || kept > cap;
+  const long long n = kept < cap ? kept : cap;
+  if (n > 0) {
+    if (n > net->hstage_cap) {
+      if (net->hstage) cudaFreeHost(net->hstage);
+      net->hstage = nullptr;
+      net->hstage_cap = 0;
+      const long long want = std::max<long long>(n, 1 << 16);
+      SNN_CUDA(net, cudaMallocHost(&net->hstage, (size_t)want * 8));
+      net->hstage_cap = want;
     }
-    std::vector<unsigned long long> h((size_t)width * net->update_grid);
-    SNN_CUDA(net, cudaMemcpy2DAsync(h.data(), (size_t)width * 8, net->rec,
-                                    (size_t)net->rec_region * 8, (size_t)width * 8,
-                                    (size_t)net->update_grid, cudaMemcpyDeviceToHost, net->stream));
+    SNN_CUDA(net, cudaMemcpyAsync(net->hstage, net->stage, (size_t)n * 8, cudaMemcpyDeviceToHost,
+                                  net->stream));
     SNN_CUDA(net, cudaStreamSynchronize(net->stream));
-    std::vector<unsigned long long> all;
-    all.reserve((size_t)kept);
-    for (int b = 0; b < net->update_grid; ++b) {
-      const long long k = (long long)cnt[b] < net->rec_region ? (long long)cnt[b] : net->rec_region;
-      all.insert(all.end(), h.begin() + (size_t)b * width, h.begin() + (size_t)b * width + k);
-    }
-    std::sort(all.begin(), all.end());
-    const long long n = kept < cap ? kept : cap;
-    if (kept > cap) lost = true;
+    // each region is in step order: a counting sort by step puts the window
+    // in step order (within a step the order stays unspecified)
+    const unsigned long long* h = net->hstage;
+    uint32_t tmin = 0xFFFFFFFFu, tmax = 0u;
     for (long long k = 0; k < n; ++k) {
-      steps[k] = (int32_t)(all[k] >> 32);
-      ids[k] = (int32_t)(all[k] & 0xFFFFFFFFull);
+      const uint32_t t = (uint32_t)(h[k] >> 32);
+      tmin = t < tmin ? t : tmin;
+      tmax = t > tmax ? t : tmax;
+    }
+    if (tmin == tmax) {
+      for (long long k = 0; k < n; ++k) {
+        steps[k] = (int32_t)tmin;
+        ids[k] = (int32_t)(h[k] & 0xFFFFFFFFull);
+      }
+    } else {
+      std::vector<long long> pos((size_t)(tmax - tmin) + 2, 0);
+      for (long long k = 0; k < n; ++k) ++pos[(size_t)((uint32_t)(h[k] >> 32) - tmin) + 1];
+      for (size_t i = 1; i < pos.size(); ++i) pos[i] += pos[i - 1];
+      for (long long k = 0; k < n; ++k) {
+        const uint32_t t = (uint32_t)(h[k] >> 32);
+        const long long o = pos[t - tmin]++;
+        steps[o] = (int32_t)t;
+        ids[o] = (int32_t)(h[k] & 0xFFFFFFFFull);
+      }
     }
     *n_out = n;
   }
-  rc = reset_records(net);
-  if (rc) return rc;
   if (lost) return fail(net, SNN_EOVERFLOW, "spike records dropped (buffer or cap too small)");
   return SNN_OK;
 }
@@ -536,10 +559,19 @@ int snn_set_record_capacity(snn_net* net, int64_t capacity) {
     cudaGetLastError();
     return cuda_fail(net, e, "cudaMalloc record buffer");
   }
+  unsigned long long* ns = nullptr;
+  e = cudaMalloc(&ns, (size_t)region * net->update_grid * 8);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(nr);
+    return cuda_fail(net, e, "cudaMalloc record staging buffer");
+  }
   cudaFree(net->rec);
-  net->device_bytes -= (size_t)net->rec_region * net->update_grid * 8;
-  net->device_bytes += (size_t)region * net->update_grid * 8;
+  cudaFree(net->stage);
+  net->device_bytes -= 2 * (size_t)net->rec_region * net->update_grid * 8;
+  net->device_bytes += 2 * (size_t)region * net->update_grid * 8;
   net->rec = nr;
+  net->stage = ns;
   net->rec_cap = capacity;
   net->rec_region = region;
   fill_step_params(net);

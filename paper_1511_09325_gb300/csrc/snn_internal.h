@@ -130,6 +130,11 @@ cudaError_t launch_update(const StepParams& p, int grid, cudaStream_t st);
 int update_grid(long long N, int num_sms);
 cudaError_t launch_deliver(const StepParams& p, int precision, int grid, cudaStream_t st);
 int deliver_grid(int precision, int num_sms, int npc, bool agg);
+// Compact the per-block record regions into stage and reset them; header[0] =
+// records kept, header[1] = 1 if records were dropped.
+cudaError_t launch_drain_records(const StepParams& p, int nreg, unsigned long long* pre,
+                                 unsigned long long* stage, unsigned long long* header,
+                                 cudaStream_t st);
 cudaError_t launch_sum_parts(const unsigned long long* part, int n, unsigned long long* out,
                              cudaStream_t st);
 

@@ -19,7 +19,7 @@
 //   items of the last d_max steps form one virtual list, split evenly over a
 //   persistent grid.  A warp takes 32 consecutive items: lane e resolves item
 //   e, then the warp streams the concatenated buckets in 16-byte chunks (4
-//   synapses per lane, two chunks in flight).  The item a chunk belongs to is
+//   synapses per lane, four chunks in flight).  The item a chunk belongs to is
 //   found from a ballot over the items' start offsets and the item's fields
 //   travel by shuffle, so the inner loop reads no shared memory.  Each
 //   synapse's weight goes to L2 as a fire-and-forget int32 reduction, except
@@ -37,6 +37,7 @@ namespace {
 
 constexpr int kUpdateThreads = 256;
 constexpr int kDeliverThreads = 256;
+constexpr int kInflight = 4;  // 16-byte synapse chunks in flight per lane
 constexpr int kTile = kUpdateThreads * 4;    // neurons per update tile
 constexpr int kSpikeBuf = 3 * kTile;         // block-local spike buffer
 constexpr int kTileCols = kTile / 2 + 2;     // columns a tile can touch (npc >= 2)
@@ -341,13 +342,13 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
                    __all_sync(0xFFFFFFFFu, !mine || colc == col0);
   int32_t* w = agg ? win : nullptr;
 
-  for (int f0 = 0; f0 < T; f0 += 256) {
-    uint32_t code[2][4], wbits[2][4];
-    float wsl[2];
-    uint32_t cxl[2];
-    bool in[2];
+  for (int f0 = 0; f0 < T; f0 += 128 * kInflight) {
+    uint32_t code[kInflight][4], wbits[kInflight][4];
+    float wsl[kInflight];
+    uint32_t cxl[kInflight];
+    bool in[kInflight];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < kInflight; ++u) {
       const int fu = f0 + u * 128;
       in[u] = false;
       wsl[u] = 0.f;
@@ -389,7 +390,7 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
       }
     }
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < kInflight; ++u) {
       if (in[u]) {
 #pragma unroll
         for (int qd = 0; qd < 4; ++qd)
@@ -478,6 +479,72 @@ __global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepPara
   }
 }
 
+// Spike-record drain, first kernel (one block): pre[b] = records kept in the
+// regions before b; header[0] = records kept, header[1] = 1 if any were
+// dropped; clears the overflow flag.
+__global__ void __launch_bounds__(1024) scan_records_kernel(const unsigned long long* rcnt,
+                                                            int nreg, long long region, Ctl* ctl,
+                                                            unsigned long long* pre,
+                                                            unsigned long long* header) {
+  __shared__ unsigned long long s_w[32];
+  __shared__ unsigned s_l[32];
+  const int per = (nreg + blockDim.x - 1) / blockDim.x;
+  const int r0 = threadIdx.x * per;
+  unsigned long long mine = 0ull;
+  unsigned lost = 0u;
+  for (int r = r0; r < r0 + per && r < nreg; ++r) {
+    const unsigned long long v = rcnt[r];
+    mine += (long long)v < region ? v : (unsigned long long)region;
+    lost |= (long long)v > region ? 1u : 0u;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lost |= __shfl_xor_sync(0xFFFFFFFFu, lost, o);
+  if (lane == 31) {
+    s_w[w] = incl;
+    s_l[w] = lost;
+  }
+  __syncthreads();
+  unsigned long long before = 0ull;
+  unsigned any = 0u;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+    if (k < w) before += s_w[k];
+    any |= s_l[k];
+  }
+  unsigned long long run = before + incl - mine;
+  for (int r = r0; r < r0 + per && r < nreg; ++r) {
+    pre[r] = run;
+    const unsigned long long v = rcnt[r];
+    run += (long long)v < region ? v : (unsigned long long)region;
+  }
+  if (threadIdx.x == blockDim.x - 1) {
+    header[0] = before + incl;
+    header[1] = (any || ctl->rec_overflow) ? 1ull : 0ull;
+    ctl->rec_overflow = 0u;
+  }
+}
+
+// Spike-record drain, second kernel: block b copies the records kept in
+// region b to stage[pre[b] ...] and empties the region.
+__global__ void copy_records_kernel(unsigned long long* rcnt, long long region,
+                                    const unsigned long long* rec, const unsigned long long* pre,
+                                    unsigned long long* stage) {
+  const int b = blockIdx.x;
+  const unsigned long long v = rcnt[b];
+  const long long kept = (long long)v < region ? (long long)v : region;
+  const unsigned long long* src = rec + (long long)b * region;
+  unsigned long long* dst = stage + pre[b];
+  for (long long k = threadIdx.x; k < kept; k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+  if (threadIdx.x == 0) rcnt[b] = 0ull;
+}
+
 // Sum of the per-block spike counts (measurement helper).
 __global__ void sum_parts_kernel(const unsigned long long* part, int n, unsigned long long* out) {
   unsigned long long s = 0ull;
@@ -532,6 +599,16 @@ cudaError_t launch_deliver(const StepParams& p, int precision, int grid, cudaStr
     deliver_kernel<SNN_EXACT_F16W><<<grid, kDeliverThreads, smem, st>>>(p);
   else
     deliver_kernel<SNN_EXACT_F32W><<<grid, kDeliverThreads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drain_records(const StepParams& p, int nreg, unsigned long long* pre,
+                                 unsigned long long* stage, unsigned long long* header,
+                                 cudaStream_t st) {
+  scan_records_kernel<<<1, 1024, 0, st>>>(p.rcnt, nreg, p.rec_region, p.ctl, pre, header);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  copy_records_kernel<<<nreg, 256, 0, st>>>(p.rcnt, p.rec_region, p.rec, pre, stage);
   return cudaGetLastError();
 }
 

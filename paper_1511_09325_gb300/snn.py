@@ -143,6 +143,14 @@ def snn_read_spikes(handle, cap=None):
     return st[:n.value], ids[:n.value], rc == SNN_EOVERFLOW
 
 
+def snn_read_spikes_into(handle, steps, ids):
+    """Drain into preallocated int32 arrays; returns (count, overflowed)."""
+    n = ctypes.c_int64()
+    rc = _check(load().snn_read_spikes(handle, _p(steps), _p(ids), int(min(len(steps), len(ids))),
+                                       ctypes.byref(n)), handle, ok=(SNN_OK, SNN_EOVERFLOW))
+    return n.value, rc == SNN_EOVERFLOW
+
+
 def snn_set_record_capacity(handle, capacity):
     _check(load().snn_set_record_capacity(handle, int(capacity)), handle)
 
@@ -228,6 +236,9 @@ class Net:
 
     def spikes(self, cap=None):
         return snn_read_spikes(self.handle, cap)
+
+    def spikes_into(self, steps, ids):
+        return snn_read_spikes_into(self.handle, steps, ids)
 
     def rates(self):
         return snn_read_rates(self.handle, self.n_cols)
