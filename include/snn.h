@@ -216,6 +216,62 @@ int snn_update_noalloc(int grid_w, int grid_h, const snn_neuron_params* neuron,
                        int64_t* n_spikes, int64_t* ext_events,
                        unsigned long long* col_counts, void* cuda_stream);
 
+/*
+ * Batched form: many independent nets advanced together by one persistent
+ * launch.  The paper runs one network on many processes (Sec. 2); a batch is
+ * the other way round -- seed sweeps or stimulus sweeps of small networks that
+ * alone would leave most of the GPU idle.  Every member computes exactly what
+ * it computes alone (same kernels' blocks, bit-identical rasters).
+ */
+typedef struct snn_batch snn_batch; /* opaque, library-owned */
+
+/*
+ * snn_batch_build -- n_nets (1..256) nets on the current device: net k is a
+ * grid_w[k] x grid_h[k] grid with neuron[k], synapse[k] and seeds[k] (as in
+ * snn_build); all nets use `precision`.  Members are owned by the batch and
+ * share its stream (cuda_stream, or a stream of its own when NULL).
+ */
+int snn_batch_build(int n_nets, const int32_t* grid_w, const int32_t* grid_h,
+                    const snn_neuron_params* neuron, const snn_synapse_params* synapse,
+                    const uint64_t* seeds, int precision, void* cuda_stream,
+                    snn_batch** out);
+
+/*
+ * snn_batch_step -- advance every member n_steps steps in one cooperative
+ * launch: each step runs all members' update blocks, a grid barrier, all
+ * members' delivery blocks and a second barrier.  Barrier waits are bounded;
+ * a wait that gives up ends the launch and the call returns SNN_ETIMEOUT (the
+ * members' state is then undefined).  Synchronises the batch's stream.
+ */
+int snn_batch_step(snn_batch* batch, int64_t n_steps);
+
+/* snn_batch_net -- member k, for snn_read_spikes / snn_read_rates /
+ * snn_stats / snn_get_state / snn_read_synapses / snn_info (snn_step and
+ * snn_step_profiled refuse a member with SNN_ESTATE).  NULL if k is out of
+ * range.  The member stays owned by the batch. */
+snn_net* snn_batch_net(snn_batch* batch, int k);
+
+/*
+ * snn_batch_tune -- pick the fastest delivery schedule for this batch (16-byte
+ * chunks in flight per lane: 4 or 2; per-warp shared windows: on or off) by
+ * timing two interleaved rounds of steps_per_trial steps of each.  The trial
+ * steps advance the simulation (all schedules compute identical sums).
+ * *choice (may be NULL) receives the pick, 0..3.
+ */
+int snn_batch_tune(snn_batch* batch, int64_t steps_per_trial, int32_t* choice);
+
+/* snn_batch_set_wait -- barrier wait bound (polls of ~64 ns, default 2^25)
+ * and, for tests of the timeout path only, arrivals the barrier waits for
+ * beyond the launched grid (default 0). */
+int snn_batch_set_wait(snn_batch* batch, int64_t spin_limit, int32_t extra_arrivals);
+
+/* snn_batch_last_error -- message of the last failure on batch (thread-local
+ * when batch is NULL). */
+const char* snn_batch_last_error(const snn_batch* batch);
+
+/* snn_batch_destroy -- free the batch and its members; NULL is a no-op. */
+void snn_batch_destroy(snn_batch* batch);
+
 /* snn_last_error -- message of the last failure on net (thread-local when net
  * is NULL).  Never NULL; valid until the next call on the same net. */
 const char* snn_last_error(const snn_net* net);

@@ -54,6 +54,7 @@ struct snn_net {
   cudaGraphExec_t graph_many = nullptr;
   int graph_many_steps = 64;
   long long rate_window_start = 0;
+  bool in_batch = false;  // stepped only through its snn_batch
   std::string err;
 };
 
@@ -376,6 +377,7 @@ int snn_build(int grid_w, int grid_h, const snn_neuron_params* neuron,
 
 int snn_step(snn_net* net, int64_t n_steps) {
   if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
+  if (net->in_batch) return fail(net, SNN_ESTATE, "net belongs to a batch: use snn_batch_step");
   if (n_steps < 0) return fail(net, SNN_EINVAL, "n_steps must be >= 0");
   if (n_steps == 0) return SNN_OK;
   int rc;
@@ -394,6 +396,7 @@ int snn_step(snn_net* net, int64_t n_steps) {
 
 int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes) {
   if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
+  if (net->in_batch) return fail(net, SNN_ESTATE, "net belongs to a batch: use snn_batch_step");
   if (n_steps < 0) return fail(net, SNN_EINVAL, "n_steps must be >= 0");
   std::vector<cudaEvent_t> ev((size_t)n_steps * 3 + 1);
   unsigned long long* dspk = nullptr;  // spikes so far, after each step
@@ -721,5 +724,240 @@ void snn_destroy(snn_net* net) {
   release(net);
   delete net;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched form: independent nets advanced together by one persistent launch.
+// ---------------------------------------------------------------------------
+struct snn_batch {
+  std::vector<snn_net*> nets;
+  int precision = 0, num_sms = 0, max_npc = 0;
+  int infl = 4;            // 16-byte chunks in flight in the delivery loop
+  int agg = 1;             // per-warp windows
+  int choice = -1;         // autotuner's pick (-1: not tuned)
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  StepParams* d_nets = nullptr;
+  int* d_first = nullptr;  // [2][n + 1]: update, delivery virtual blocks
+  unsigned* d_bar = nullptr;
+  long long t = 0;
+  long long spin_limit = 1LL << 25;
+  unsigned extra_arrivals = 0u;
+  std::string err;
+};
+
+namespace {
+
+int bfail(snn_batch* b, int code, const std::string& msg) {
+  if (b)
+    b->err = msg;
+  else
+    g_err = msg;
+  return code;
+}
+
+#define SNN_BCUDA(b, call)                                                            \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return bfail((b), SNN_ECUDA, std::string(#call ": ") +     \
+                                                           cudaGetErrorString(e_));   \
+  } while (0)
+
+void batch_release(snn_batch* b) {
+  for (snn_net* n : b->nets) snn_destroy(n);
+  b->nets.clear();
+  if (b->d_nets) cudaFree(b->d_nets);
+  if (b->d_first) cudaFree(b->d_first);
+  if (b->d_bar) cudaFree(b->d_bar);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+// Upload the members' step parameters with the batch's window setting.
+int batch_upload(snn_batch* b) {
+  std::vector<StepParams> ps(b->nets.size());
+  for (size_t k = 0; k < b->nets.size(); ++k) {
+    b->nets[k]->agg = b->agg != 0;
+    fill_step_params(b->nets[k]);
+    ps[k] = b->nets[k]->sp;
+  }
+  SNN_BCUDA(b, cudaMemcpyAsync(b->d_nets, ps.data(), ps.size() * sizeof(StepParams),
+                               cudaMemcpyHostToDevice, b->stream));
+  SNN_BCUDA(b, cudaStreamSynchronize(b->stream));
+  return SNN_OK;
+}
+
+int batch_run(snn_batch* b, long long n_steps) {
+  if (n_steps == 0) return SNN_OK;
+  // members' buffers may have been reallocated (record capacity): refresh
+  const int urc = batch_upload(b);
+  if (urc != SNN_OK) return urc;
+  const int n = (int)b->nets.size();
+  BatchParams bp{};
+  bp.nets = b->d_nets;
+  bp.u_first = b->d_first;
+  bp.d_first = b->d_first + (n + 1);
+  bp.n_nets = n;
+  bp.t0 = b->t;
+  bp.n_steps = n_steps;
+  bp.bar = b->d_bar;
+  bp.spin_limit = b->spin_limit;
+  bp.extra_arrivals = b->extra_arrivals;
+  const int grid = batch_grid(b->precision, b->infl, b->num_sms, b->max_npc);
+  if (grid < 1) return bfail(b, SNN_ECUDA, "batch kernel does not fit on the device");
+  SNN_BCUDA(b, cudaMemsetAsync(b->d_bar, 0, 3 * sizeof(unsigned), b->stream));
+  SNN_BCUDA(b, launch_batch(bp, b->precision, b->infl, grid, b->max_npc, b->stream));
+  unsigned flags[3] = {0u, 0u, 0u};
+  SNN_BCUDA(b, cudaMemcpyAsync(flags, b->d_bar, sizeof(flags), cudaMemcpyDeviceToHost, b->stream));
+  SNN_BCUDA(b, cudaStreamSynchronize(b->stream));
+  if (flags[2]) return bfail(b, SNN_ETIMEOUT, "a grid barrier wait gave up");
+  b->t += n_steps;
+  return SNN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int snn_batch_build(int n_nets, const int32_t* grid_w, const int32_t* grid_h,
+                    const snn_neuron_params* neuron, const snn_synapse_params* synapse,
+                    const uint64_t* seeds, int precision, void* cuda_stream, snn_batch** out) {
+  if (!out) return bfail(nullptr, SNN_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_nets < 1 || n_nets > kMaxBatch) return bfail(nullptr, SNN_EINVAL, "n_nets must be in 1..256");
+  if (!grid_w || !grid_h || !neuron || !synapse || !seeds)
+    return bfail(nullptr, SNN_EINVAL, "null argument");
+  for (int k = 0; k < n_nets; ++k) {
+    std::string why;
+    const int rc = validate(grid_w[k], grid_h[k], neuron + k, synapse + k, precision, &why);
+    if (rc != SNN_OK) return bfail(nullptr, rc, "net " + std::to_string(k) + ": " + why);
+  }
+  snn_batch* b = new (std::nothrow) snn_batch();
+  if (!b) return bfail(nullptr, SNN_ENOMEM, "host allocation failed");
+  b->precision = precision;
+  if (cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete b;
+      return bfail(nullptr, SNN_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    b->own_stream = true;
+  }
+  int rc = SNN_OK;
+  std::vector<int> first(2 * (size_t)(n_nets + 1), 0);
+  for (int k = 0; k < n_nets && rc == SNN_OK; ++k) {
+    snn_net* net = nullptr;
+    rc = snn_build(grid_w[k], grid_h[k], neuron + k, synapse + k, seeds[k], precision, b->stream,
+                   &net);
+    if (rc != SNN_OK) break;
+    net->in_batch = true;
+    b->nets.push_back(net);
+    b->max_npc = std::max(b->max_npc, net->npc);
+    b->num_sms = net->num_sms;
+    // update: the net's own grid (its partial sums and record regions);
+    // delivery: 8 virtual blocks per column, at most the standalone grid
+    first[k + 1] = first[k] + net->update_grid;
+    const long long dg = std::min<long long>(net->deliver_grid, std::max<long long>(1, 8 * net->ncol));
+    first[(n_nets + 1) + k + 1] = first[(n_nets + 1) + k] + (int)dg;
+  }
+  if (rc != SNN_OK) {
+    const std::string why = g_err;
+    batch_release(b);
+    delete b;
+    return bfail(nullptr, rc, why);
+  }
+  cudaError_t e = cudaMalloc(&b->d_nets, sizeof(StepParams) * (size_t)n_nets);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_first, first.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, 4 * sizeof(unsigned));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_first, first.data(), first.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    batch_release(b);
+    delete b;
+    return bfail(nullptr, e == cudaErrorMemoryAllocation ? SNN_ENOMEM : SNN_ECUDA,
+                 std::string("batch buffers: ") + cudaGetErrorString(e));
+  }
+  rc = batch_upload(b);
+  if (rc != SNN_OK) {
+    const std::string why = b->err;
+    batch_release(b);
+    delete b;
+    return bfail(nullptr, rc, why);
+  }
+  *out = b;
+  return SNN_OK;
+}
+
+int snn_batch_step(snn_batch* b, int64_t n_steps) {
+  if (!b) return bfail(nullptr, SNN_EINVAL, "batch is NULL");
+  if (n_steps < 0) return bfail(b, SNN_EINVAL, "n_steps must be >= 0");
+  return batch_run(b, n_steps);
+}
+
+snn_net* snn_batch_net(snn_batch* b, int k) {
+  if (!b || k < 0 || k >= (int)b->nets.size()) return nullptr;
+  return b->nets[k];
+}
+
+int snn_batch_tune(snn_batch* b, int64_t steps_per_trial, int32_t* choice) {
+  if (!b || steps_per_trial < 1) return bfail(b, SNN_EINVAL, "bad argument");
+  // every variant computes the same sums, so the trials simply advance the
+  // simulation; two interleaved rounds even out changes in activity
+  const int infl[4] = {4, 4, 2, 2}, agg[4] = {1, 0, 1, 0};
+  double ms[4] = {0, 0, 0, 0};
+  cudaEvent_t e0, e1;
+  SNN_BCUDA(b, cudaEventCreate(&e0));
+  SNN_BCUDA(b, cudaEventCreate(&e1));
+  int rc = SNN_OK;
+  for (int round = 0; round < 2 && rc == SNN_OK; ++round) {
+    for (int v = 0; v < 4 && rc == SNN_OK; ++v) {
+      b->infl = infl[v];
+      b->agg = agg[v];
+      rc = batch_upload(b);
+      if (rc) break;
+      cudaEventRecord(e0, b->stream);
+      rc = batch_run(b, steps_per_trial);
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float x = 0.f;
+      cudaEventElapsedTime(&x, e0, e1);
+      ms[v] += x;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SNN_OK) return rc;
+  int best = 0;
+  for (int v = 1; v < 4; ++v)
+    if (ms[v] < ms[best]) best = v;
+  b->infl = infl[best];
+  b->agg = agg[best];
+  b->choice = best;
+  rc = batch_upload(b);
+  if (rc) return rc;
+  if (choice) *choice = best;
+  return SNN_OK;
+}
+
+int snn_batch_set_wait(snn_batch* b, int64_t spin_limit, int32_t extra_arrivals) {
+  if (!b || spin_limit < 1 || extra_arrivals < 0) return bfail(b, SNN_EINVAL, "bad argument");
+  b->spin_limit = spin_limit;
+  b->extra_arrivals = (unsigned)extra_arrivals;
+  return SNN_OK;
+}
+
+const char* snn_batch_last_error(const snn_batch* b) { return b ? b->err.c_str() : g_err.c_str(); }
+
+void snn_batch_destroy(snn_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_release(b);
+  delete b;
+}
+
 
 }  // extern "C"

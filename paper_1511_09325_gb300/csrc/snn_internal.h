@@ -107,6 +107,19 @@ struct StepParams {
   unsigned long long* spk_part;  // spike partial sums, one per update block
 };
 
+// A batch of nets advanced by one persistent launch (snn_batch_*).
+constexpr int kMaxBatch = 256;
+struct BatchParams {
+  StepParams* nets;         // [n_nets], device
+  const int* u_first;       // [n_nets + 1] first update virtual block of each net
+  const int* d_first;       // [n_nets + 1] first delivery virtual block of each net
+  int n_nets;
+  long long t0, n_steps;
+  unsigned* bar;            // grid barrier: arrivals, generation, error flag
+  long long spin_limit;     // polls before a barrier wait gives up
+  unsigned extra_arrivals;  // arrivals expected beyond the grid (0; tests only)
+};
+
 struct BuildParams {
   long long N;
   int npc, nexc, W, H, K, k_local, dmin, ndel, rowcap, n_off;
@@ -135,6 +148,10 @@ int deliver_grid(int precision, int num_sms, int npc, bool agg);
 cudaError_t launch_drain_records(const StepParams& p, int nreg, unsigned long long* pre,
                                  unsigned long long* stage, unsigned long long* header,
                                  cudaStream_t st);
+size_t batch_smem(int max_npc);
+int batch_grid(int precision, int infl, int num_sms, int max_npc);
+cudaError_t launch_batch(const BatchParams& b, int precision, int infl, int grid, int max_npc,
+                         cudaStream_t st);
 cudaError_t launch_sum_parts(const unsigned long long* part, int n, unsigned long long* out,
                              cudaStream_t st);
 

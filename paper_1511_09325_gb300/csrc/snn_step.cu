@@ -90,22 +90,32 @@ __device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
                : "memory");
 }
 
+// Shared memory of one update block.
+struct UpdateSmem {
+  uint32_t buf[kSpikeBuf];       // spikes of the tiles since the last flush
+  uint32_t thr[kMaxPoisThr + 1];  // Poisson thresholds
+  uint8_t guide[256];            // Poisson guide table
+  unsigned tpop[kTileCols][2];   // E / I spikes per column of the tile
+  unsigned tpos[kTileCols];      // buffer offset of each column's spikes
+  unsigned fill, base;
+  unsigned long long rc, spk;
+  unsigned ksum[kUpdateThreads / 32];
+};
+
 // Append the block's buffered spikes to the step's list (one atomic) and to
-// the block's own region of the record buffer (step << 32 | id).
-__device__ __forceinline__ void flush_spikes(const StepParams& P, long long t, int slot,
-                                             uint32_t* s_buf, unsigned* s_fill,
-                                             unsigned* s_base, unsigned long long* s_rc,
-                                             unsigned long long* s_spk) {
-  const unsigned n = *s_fill;  // block-uniform (read after a barrier)
+// the block's own region `vb` of the record buffer (step << 32 | id).
+__device__ __forceinline__ void flush_spikes(const StepParams& P, long long t, int slot, int vb,
+                                             UpdateSmem& S) {
+  const unsigned n = S.fill;  // block-uniform (read after a barrier)
   if (n == 0u) return;
-  if (threadIdx.x == 0) *s_base = atomicAdd(P.cnt + slot, n);
+  if (threadIdx.x == 0) S.base = atomicAdd(P.cnt + slot, n);
   __syncthreads();
-  const unsigned base = *s_base;
-  const unsigned long long rc = *s_rc;
+  const unsigned base = S.base;
+  const unsigned long long rc = S.rc;
   uint32_t* list = P.ids + (long long)slot * P.N + base;
-  unsigned long long* region = P.rec + (long long)blockIdx.x * P.rec_region;
+  unsigned long long* region = P.rec + (long long)vb * P.rec_region;
   for (unsigned e = threadIdx.x; e < n; e += blockDim.x) {
-    const uint32_t id = s_buf[e];
+    const uint32_t id = S.buf[e];
     list[e] = id;
     const unsigned long long ri = rc + e;
     if ((long long)ri < P.rec_region) region[ri] = ((unsigned long long)(unsigned)t << 32) | id;
@@ -113,46 +123,39 @@ __device__ __forceinline__ void flush_spikes(const StepParams& P, long long t, i
   __syncthreads();
   if (threadIdx.x == 0) {
     if ((long long)(rc + n) > P.rec_region) P.ctl->rec_overflow = 1u;
-    *s_rc = rc + n;
-    *s_spk += n;
-    *s_fill = 0u;
+    S.rc = rc + n;
+    S.spk += n;
+    S.fill = 0u;
   }
   __syncthreads();
 }
 
-// Grid-stride over tiles; the grid size is fixed per net, so block b owns
-// ext_part[b], spk_part[b] and record region b.
-__global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams P) {
-  __shared__ uint32_t s_buf[kSpikeBuf];
-  __shared__ uint32_t s_thr[kMaxPoisThr + 1];
-  __shared__ uint8_t s_guide[256];
-  __shared__ unsigned s_tpop[kTileCols][2];  // E / I spikes per column of the tile
-  __shared__ unsigned s_tpos[kTileCols];     // buffer offset of each column's spikes
-  __shared__ unsigned s_fill, s_base;
-  __shared__ unsigned long long s_rc, s_spk;
-  __shared__ unsigned s_ksum[kUpdateThreads / 32];
-
-  const long long t = P.ctl->t;
+// Update block vb of vgrid for step t: tiles vb, vb + vgrid, ...  Block vb
+// owns ext_part[vb], spk_part[vb] and record region vb of the net, so the
+// grid size must be the same every step.
+__device__ __forceinline__ void update_body(const StepParams& P, long long t, int vb, int vgrid,
+                                            UpdateSmem& S) {
+  __syncthreads();  // the shared memory may still be read by a previous body
   const int slot = (int)(t % P.nslot);
-  for (int m = threadIdx.x; m < 256; m += blockDim.x) s_guide[m] = P.pois_guide[m];
-  for (int m = threadIdx.x; m <= kMaxPoisThr; m += blockDim.x) s_thr[m] = P.pois_thr[m];
+  for (int m = threadIdx.x; m < 256; m += blockDim.x) S.guide[m] = P.pois_guide[m];
+  for (int m = threadIdx.x; m <= kMaxPoisThr; m += blockDim.x) S.thr[m] = P.pois_thr[m];
   if (threadIdx.x == 0) {
-    s_fill = 0u;
-    s_rc = P.rcnt[blockIdx.x];
-    s_spk = 0ull;
+    S.fill = 0u;
+    S.rc = P.rcnt[vb];
+    S.spk = 0ull;
   }
   unsigned ksum = 0u;
   const long long quads = (P.N + 3) / 4;
   const long long tiles = (quads + kUpdateThreads - 1) / kUpdateThreads;
 
-  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+  for (long long tile = vb; tile < tiles; tile += vgrid) {
     const long long first = tile * kTile;
     const long long last = (first + kTile < P.N ? first + kTile : P.N) - 1;
     const int col0 = (int)(first / P.npc);
     const int ncols = (int)(last / P.npc) - col0 + 1;
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
-      s_tpop[k][0] = 0u;
-      s_tpop[k][1] = 0u;
+      S.tpop[k][0] = 0u;
+      S.tpop[k][1] = 0u;
     }
     __syncthreads();
 
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
       int l = (int)(i0 - (long long)col * P.npc);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const int k = poisson_count(xin[e], s_guide, s_thr, P.n_pois_thr);
+        const int k = poisson_count(xin[e], S.guide, S.thr, P.n_pois_thr);
         const int32_t I = ain[e] + k * P.jx;
         const bool exc = l < P.nexc;
         const NeuronOut o = neuron_step(vin[e], cin[e], rin[e], I, exc ? P.pvc_e : P.pvc_i, P);
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
           ksum += (unsigned)k;
           if (o.spike) {
             scol[e] = col - col0;
-            rank[e] = atomicAdd(&s_tpop[col - col0][exc ? 0 : 1], 1u);
+            rank[e] = atomicAdd(&S.tpop[col - col0][exc ? 0 : 1], 1u);
             if (!exc) rank[e] |= 0x80000000u;  // ranked among the column's I spikes
           }
         }
@@ -207,12 +210,12 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
     // place the tile's spikes in the buffer grouped by column (E then I), so
     // that neighbouring list entries share a column
     if (threadIdx.x == 0) {
-      unsigned pos = s_fill;
+      unsigned pos = S.fill;
       for (int k = 0; k < ncols; ++k) {
-        s_tpos[k] = pos;
-        pos += s_tpop[k][0] + s_tpop[k][1];
+        S.tpos[k] = pos;
+        pos += S.tpop[k][0] + S.tpop[k][1];
       }
-      s_fill = pos;
+      S.fill = pos;
     }
     __syncthreads();
 #pragma unroll
@@ -220,33 +223,37 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
       if (scol[e] >= 0) {
         const int k = scol[e];
         const unsigned r = rank[e] & 0x7FFFFFFFu;
-        const unsigned off = (rank[e] & 0x80000000u) ? s_tpop[k][0] + r : r;
-        s_buf[s_tpos[k] + off] = (uint32_t)(i0 + e);
+        const unsigned off = (rank[e] & 0x80000000u) ? S.tpop[k][0] + r : r;
+        S.buf[S.tpos[k] + off] = (uint32_t)(i0 + e);
       }
     }
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
-      if (s_tpop[k][0]) atomicAdd(&P.colcnt[2 * (col0 + k)], (unsigned long long)s_tpop[k][0]);
-      if (s_tpop[k][1]) atomicAdd(&P.colcnt[2 * (col0 + k) + 1], (unsigned long long)s_tpop[k][1]);
+      if (S.tpop[k][0]) atomicAdd(&P.colcnt[2 * (col0 + k)], (unsigned long long)S.tpop[k][0]);
+      if (S.tpop[k][1]) atomicAdd(&P.colcnt[2 * (col0 + k) + 1], (unsigned long long)S.tpop[k][1]);
     }
     __syncthreads();
-    if (s_fill > (unsigned)(kSpikeBuf - kTile))
-      flush_spikes(P, t, slot, s_buf, &s_fill, &s_base, &s_rc, &s_spk);
+    if (S.fill > (unsigned)(kSpikeBuf - kTile)) flush_spikes(P, t, slot, vb, S);
   }
   __syncthreads();
-  flush_spikes(P, t, slot, s_buf, &s_fill, &s_base, &s_rc, &s_spk);
+  flush_spikes(P, t, slot, vb, S);
 
   // external events: per-block partial sum, no atomics
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ksum += __shfl_xor_sync(0xFFFFFFFFu, ksum, o);
-  if ((threadIdx.x & 31) == 0) s_ksum[threadIdx.x >> 5] = ksum;
+  if ((threadIdx.x & 31) == 0) S.ksum[threadIdx.x >> 5] = ksum;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long tot = 0ull;
-    for (int w = 0; w < kUpdateThreads / 32; ++w) tot += s_ksum[w];
-    P.ext_part[blockIdx.x] += tot;
-    P.spk_part[blockIdx.x] += s_spk;
-    P.rcnt[blockIdx.x] = s_rc;
+    for (int w = 0; w < kUpdateThreads / 32; ++w) tot += S.ksum[w];
+    P.ext_part[vb] += tot;
+    P.spk_part[vb] += S.spk;
+    P.rcnt[vb] = S.rc;
   }
+}
+
+__global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams P) {
+  __shared__ UpdateSmem S;
+  update_body(P, P.ctl->t, (int)blockIdx.x, (int)gridDim.x, S);
 }
 
 // Periodic coordinate v in [-3, n + 3); one conditional correction suffices
@@ -288,7 +295,7 @@ __device__ __forceinline__ void deliver_record(uint32_t code, uint32_t wbits, fl
 }
 
 // One warp, one batch of up to 32 consecutive items.
-template <int PREC>
+template <int PREC, int INFL>
 __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item, unsigned hi,
                                               const unsigned* s_pref, const long long* s_list,
                                               int32_t* win) {
@@ -342,13 +349,13 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
                    __all_sync(0xFFFFFFFFu, !mine || colc == col0);
   int32_t* w = agg ? win : nullptr;
 
-  for (int f0 = 0; f0 < T; f0 += 128 * kInflight) {
-    uint32_t code[kInflight][4], wbits[kInflight][4];
-    float wsl[kInflight];
-    uint32_t cxl[kInflight];
-    bool in[kInflight];
+  for (int f0 = 0; f0 < T; f0 += 128 * INFL) {
+    uint32_t code[INFL][4], wbits[INFL][4];
+    float wsl[INFL];
+    uint32_t cxl[INFL];
+    bool in[INFL];
 #pragma unroll
-    for (int u = 0; u < kInflight; ++u) {
+    for (int u = 0; u < INFL; ++u) {
       const int fu = f0 + u * 128;
       in[u] = false;
       wsl[u] = 0.f;
@@ -390,7 +397,7 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
       }
     }
 #pragma unroll
-    for (int u = 0; u < kInflight; ++u) {
+    for (int u = 0; u < INFL; ++u) {
       if (in[u]) {
 #pragma unroll
         for (int qd = 0; qd < 4; ++qd)
@@ -413,18 +420,24 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
   }
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepParams P) {
-  extern __shared__ int32_t s_win[];  // [warps][n_per_col] when P.agg
-  __shared__ unsigned s_pref[kMaxDelays + 1];
-  __shared__ long long s_list[kMaxDelays];
-  __shared__ unsigned s_next;
+struct DeliverSmem {
+  unsigned pref[kMaxDelays + 1];  // items per delay bucket, prefix
+  long long list[kMaxDelays];     // list offset per bucket
+  unsigned next;                  // next batch of this block
+};
+constexpr size_t kDeliverSmemPad = (sizeof(DeliverSmem) + 255) / 256 * 256;
 
-  const long long t = P.ctl->t;
+// Delivery block vb of vgrid for step t: items [total vb / vgrid, ...) of the
+// (bucket, spiker) list.  win: n_per_col * warps ints of shared memory for the
+// per-warp windows.
+template <int PREC, int INFL>
+__device__ __forceinline__ void deliver_body(const StepParams& P, long long t, int vb, int vgrid,
+                                             DeliverSmem& S, int32_t* win_base) {
+  __syncthreads();  // the shared memory may still be read by a previous body
   // the slot that the next update fills holds step t - d_max: no longer read
-  if (blockIdx.x == 0 && threadIdx.x == 0) P.cnt[(t + 1) % P.nslot] = 0u;
+  if (vb == 0 && threadIdx.x == 0) P.cnt[(t + 1) % P.nslot] = 0u;
   const int lane = threadIdx.x & 31;
-  int32_t* win = P.agg ? s_win + (threadIdx.x >> 5) * P.npc : nullptr;
+  int32_t* win = P.agg ? win_base + (threadIdx.x >> 5) * P.npc : nullptr;
   if (win)
     for (int l = lane; l < P.npc; l += 32) win[l] = 0;
   if (threadIdx.x < 32) {
@@ -445,26 +458,34 @@ __global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepPara
       const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
       if (b >= o) incl += v;
     }
-    s_pref[b + 1] = incl;
+    S.pref[b + 1] = incl;
     if (b == 0) {
-      s_pref[0] = 0u;
-      s_next = 0u;
+      S.pref[0] = 0u;
+      S.next = 0u;
     }
-    s_list[b] = off;
+    S.list[b] = off;
   }
   __syncthreads();
 
   // this block's contiguous share of the step's items, 32 per warp batch
-  const unsigned total = s_pref[P.ndel];
-  const unsigned lo = (unsigned)(((unsigned long long)total * blockIdx.x) / gridDim.x);
-  const unsigned hi = (unsigned)(((unsigned long long)total * (blockIdx.x + 1)) / gridDim.x);
+  const unsigned total = S.pref[P.ndel];
+  const unsigned lo = (unsigned)(((unsigned long long)total * vb) / vgrid);
+  const unsigned hi = (unsigned)(((unsigned long long)total * (vb + 1)) / vgrid);
   while (true) {
     unsigned k0 = 0u;
-    if (lane == 0) k0 = atomicAdd(&s_next, 32u);
+    if (lane == 0) k0 = atomicAdd(&S.next, 32u);
     k0 = __shfl_sync(0xFFFFFFFFu, k0, 0);
     if (lo + k0 >= hi) break;
-    deliver_batch<PREC>(P, lo + k0 + lane, hi, s_pref, s_list, win);
+    deliver_batch<PREC, INFL>(P, lo + k0 + lane, hi, S.pref, S.list, win);
   }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepParams P) {
+  extern __shared__ int32_t s_win[];  // [warps][n_per_col] when P.agg
+  __shared__ DeliverSmem S;
+  const long long t = P.ctl->t;
+  deliver_body<PREC, kInflight>(P, t, (int)blockIdx.x, (int)gridDim.x, S, s_win);
 
   // the last block to finish closes the step
   __syncthreads();
@@ -477,6 +498,111 @@ __global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepPara
       P.ctl->t = t + 1;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: many independent nets advanced by one persistent launch.
+// Every step runs the update blocks of all nets, a grid barrier, the delivery
+// blocks of all nets, and a second barrier.  Virtual block g of a phase
+// belongs to net k with first[k] <= g < first[k + 1]; each virtual block is the
+// standalone kernel's block, so every net computes exactly what its own
+// kernels compute.
+// ---------------------------------------------------------------------------
+
+// Bounded grid barrier (all blocks are co-resident: cooperative launch).  A
+// block that polls spin_limit times without the generation moving sets *err
+// and gives up; every later barrier then returns false at once.
+__device__ __forceinline__ bool grid_barrier(const BatchParams& B, unsigned* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned ok = 1u;
+    volatile unsigned* gen = B.bar + 1;
+    volatile unsigned* err = B.bar + 2;
+    if (*err) {
+      ok = 0u;
+    } else {
+      const unsigned g = *gen;
+      __threadfence();
+      const unsigned expected = gridDim.x + B.extra_arrivals;
+      if (atomicAdd(B.bar, 1u) == expected - 1u) {
+        B.bar[0] = 0u;
+        __threadfence();
+        atomicAdd(B.bar + 1, 1u);
+      } else {
+        long long polls = 0;
+        while (*gen == g) {
+          if (*err) {
+            ok = 0u;
+            break;
+          }
+          if (++polls > B.spin_limit) {
+            atomicExch(B.bar + 2, 1u);
+            ok = 0u;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+    }
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0u;
+}
+
+// Net of virtual block g: the last k with first[k] <= g.
+__device__ __forceinline__ int net_of(const int* first, int n, int g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int PREC, int INFL>
+__global__ void __launch_bounds__(kDeliverThreads, 3) batch_kernel(const BatchParams B) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  __shared__ StepParams s_p;  // the current virtual block's net
+  __shared__ int s_uf[kMaxBatch + 1], s_df[kMaxBatch + 1];
+  __shared__ unsigned s_ok;
+  UpdateSmem& SU = *reinterpret_cast<UpdateSmem*>(s_dyn);
+  DeliverSmem& SD = *reinterpret_cast<DeliverSmem*>(s_dyn);
+  int32_t* win = reinterpret_cast<int32_t*>(s_dyn + kDeliverSmemPad);
+  const int n = B.n_nets;
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) {
+    s_uf[k] = B.u_first[k];
+    s_df[k] = B.d_first[k];
+  }
+  __syncthreads();
+  const int total_u = s_uf[n], total_d = s_df[n];
+  for (long long step = 0; step < B.n_steps; ++step) {
+    const long long t = B.t0 + step;
+    for (int g = blockIdx.x; g < total_u; g += gridDim.x) {
+      const int k = net_of(s_uf, n, g);
+      __syncthreads();
+      for (int w = threadIdx.x; w < (int)(sizeof(StepParams) / 4); w += blockDim.x)
+        reinterpret_cast<uint32_t*>(&s_p)[w] = reinterpret_cast<const uint32_t*>(B.nets + k)[w];
+      __syncthreads();
+      update_body(s_p, t, g - s_uf[k], s_uf[k + 1] - s_uf[k], SU);
+    }
+    if (!grid_barrier(B, &s_ok)) return;
+    for (int g = blockIdx.x; g < total_d; g += gridDim.x) {
+      const int k = net_of(s_df, n, g);
+      __syncthreads();
+      for (int w = threadIdx.x; w < (int)(sizeof(StepParams) / 4); w += blockDim.x)
+        reinterpret_cast<uint32_t*>(&s_p)[w] = reinterpret_cast<const uint32_t*>(B.nets + k)[w];
+      __syncthreads();
+      deliver_body<PREC, INFL>(s_p, t, g - s_df[k], s_df[k + 1] - s_df[k], SD, win);
+    }
+    if (!grid_barrier(B, &s_ok)) return;
+  }
+  if (blockIdx.x == 0)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) B.nets[k].ctl->t = B.t0 + B.n_steps;
 }
 
 // Spike-record drain, first kernel (one block): pre[b] = records kept in the
@@ -610,6 +736,39 @@ cudaError_t launch_drain_records(const StepParams& p, int nreg, unsigned long lo
   if (e != cudaSuccess) return e;
   copy_records_kernel<<<nreg, 256, 0, st>>>(p.rcnt, p.rec_region, p.rec, pre, stage);
   return cudaGetLastError();
+}
+
+namespace {
+template <int PREC, int INFL>
+void* batch_fn() {
+  return reinterpret_cast<void*>(batch_kernel<PREC, INFL>);
+}
+void* batch_kernel_ptr(int precision, int infl) {
+  if (precision == SNN_EXACT_F16W) return infl == 2 ? batch_fn<1, 2>() : batch_fn<1, 4>();
+  return infl == 2 ? batch_fn<0, 2>() : batch_fn<0, 4>();
+}
+}  // namespace
+
+size_t batch_smem(int max_npc) {
+  const size_t upd = sizeof(UpdateSmem);
+  const size_t del = kDeliverSmemPad + (size_t)kDeliverWarps * (size_t)max_npc * sizeof(int32_t);
+  return upd > del ? upd : del;
+}
+
+int batch_grid(int precision, int infl, int num_sms, int max_npc) {
+  const size_t smem = batch_smem(max_npc);
+  void* fn = batch_kernel_ptr(precision, infl);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kDeliverThreads, smem);
+  return per_sm * num_sms;
+}
+
+cudaError_t launch_batch(const BatchParams& b, int precision, int infl, int grid, int max_npc,
+                         cudaStream_t st) {
+  void* args[] = {const_cast<BatchParams*>(&b)};
+  return cudaLaunchCooperativeKernel(batch_kernel_ptr(precision, infl), dim3(grid),
+                                     dim3(kDeliverThreads), args, batch_smem(max_npc), st);
 }
 
 cudaError_t launch_sum_parts(const unsigned long long* part, int n, unsigned long long* out,

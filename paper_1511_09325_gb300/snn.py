@@ -22,6 +22,8 @@ PRECISIONS = {"f32w": SNN_EXACT_F32W, "f16w": SNN_EXACT_F16W}
 EXPORTS = ("snn_build", "snn_step", "snn_read_spikes", "snn_pending_spikes",
            "snn_set_record_capacity", "snn_read_rates", "snn_stats", "snn_get_state",
            "snn_read_synapses", "snn_info", "snn_step_profiled", "snn_update_noalloc",
+           "snn_batch_build", "snn_batch_step", "snn_batch_net", "snn_batch_tune",
+           "snn_batch_set_wait", "snn_batch_last_error", "snn_batch_destroy",
            "snn_last_error", "snn_destroy")
 
 
@@ -75,12 +77,23 @@ def load(path=LIB_PATH):
     L.snn_step_profiled.argtypes = [vp, i64, vp, vp]
     L.snn_update_noalloc.argtypes = [i32, i32, P(NeuronParams), ctypes.c_uint64, i64,
                                      vp, vp, vp, vp, vp, P(i64), P(i64), vp, vp]
+    L.snn_batch_build.argtypes = [i32, vp, vp, vp, vp, vp, i32, vp, P(vp)]
+    L.snn_batch_step.argtypes = [vp, i64]
+    L.snn_batch_net.argtypes = [vp, i32]
+    L.snn_batch_net.restype = vp
+    L.snn_batch_tune.argtypes = [vp, i64, P(ctypes.c_int32)]
+    L.snn_batch_set_wait.argtypes = [vp, i64, ctypes.c_int32]
+    L.snn_batch_last_error.argtypes = [vp]
+    L.snn_batch_last_error.restype = ctypes.c_char_p
+    L.snn_batch_destroy.argtypes = [vp]
+    L.snn_batch_destroy.restype = None
     L.snn_last_error.argtypes = [vp]
     L.snn_last_error.restype = ctypes.c_char_p
     L.snn_destroy.argtypes = [vp]
     L.snn_destroy.restype = None
     for f in EXPORTS:
-        if f not in ("snn_last_error", "snn_destroy"):
+        if f not in ("snn_last_error", "snn_destroy", "snn_batch_net", "snn_batch_last_error",
+                     "snn_batch_destroy"):
             getattr(L, f).restype = i32
     _lib = L
     return L
@@ -218,6 +231,91 @@ def snn_update_noalloc(grid_w, grid_h, neuron, seed, step, v, c, refractory, inp
 def snn_destroy(handle):
     if handle:
         load().snn_destroy(handle)
+
+
+def _bcheck(rc, handle, ok=(SNN_OK,)):
+    if rc not in ok:
+        raise SnnError(rc, load().snn_batch_last_error(handle).decode())
+    return rc
+
+
+class Member:
+    """A net owned by a Batch: every read-only call of Net, no stepping."""
+
+    def __init__(self, handle, grid_w, grid_h, neuron, synapse):
+        self.handle = handle
+        self.grid_w, self.grid_h = grid_w, grid_h
+        self.n_cols = grid_w * grid_h
+        self.n = self.n_cols * neuron["n_per_col"]
+        self.k_out = synapse["k_out"]
+
+    def spikes(self, cap=None):
+        return snn_read_spikes(self.handle, cap)
+
+    def rates(self):
+        return snn_read_rates(self.handle, self.n_cols)
+
+    def stats(self):
+        return snn_stats(self.handle)
+
+    def state(self):
+        return snn_get_state(self.handle, self.n)
+
+    def info(self):
+        return snn_info(self.handle)
+
+    def set_record_capacity(self, cap):
+        snn_set_record_capacity(self.handle, cap)
+
+
+class Batch:
+    """Independent nets advanced together by one persistent launch."""
+
+    def __init__(self, grids, neurons, synapses, seeds, precision="f32w", stream=None):
+        L = load()
+        n = len(grids)
+        gw = np.array([g[0] for g in grids], np.int32)
+        gh = np.array([g[1] for g in grids], np.int32)
+        nps = (NeuronParams * n)(*[neuron_struct(x) for x in neurons])
+        sps = (SynapseParams * n)(*[synapse_struct(x) for x in synapses])
+        sd = np.array(seeds, np.uint64)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        h = ctypes.c_void_p()
+        _bcheck(L.snn_batch_build(n, _p(gw), _p(gh), ctypes.cast(nps, ctypes.c_void_p),
+                                  ctypes.cast(sps, ctypes.c_void_p), _p(sd), prec, stream,
+                                  ctypes.byref(h)), None)
+        self.handle = h.value
+        self.members = [Member(L.snn_batch_net(self.handle, k), grids[k][0], grids[k][1],
+                               neurons[k], synapses[k]) for k in range(n)]
+
+    def step(self, n_steps):
+        _bcheck(load().snn_batch_step(self.handle, int(n_steps)), self.handle)
+
+    def tune(self, steps_per_trial):
+        c = ctypes.c_int32()
+        _bcheck(load().snn_batch_tune(self.handle, int(steps_per_trial), ctypes.byref(c)), self.handle)
+        return c.value
+
+    def set_wait(self, spin_limit, extra_arrivals=0):
+        _bcheck(load().snn_batch_set_wait(self.handle, int(spin_limit), int(extra_arrivals)),
+                self.handle)
+
+    def close(self):
+        if self.handle:
+            load().snn_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Net:

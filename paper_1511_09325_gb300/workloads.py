@@ -89,3 +89,20 @@ def synapse_params(**overrides):
 
 def n_neurons(grid_w, grid_h, n_per_col=NEURON["n_per_col"]):
     return grid_w * grid_h * n_per_col
+
+
+def batch_workload(n_nets=64, seed0=100):
+    """The batched form: n_nets independent networks of the default
+    construction, grid sizes drawn uniformly from 1x1 to 8x8 columns (numpy
+    generator seeded with 1511), seeds seed0 .. seed0 + n_nets - 1, external
+    rates swept linearly over 1.5-3.5 kHz.  Returns (grids, neurons, synapses,
+    seeds)."""
+    import numpy as np
+
+    rng = np.random.default_rng(1511)
+    grids = [(int(a), int(b)) for a, b in rng.integers(1, 9, size=(n_nets, 2))]
+    rates = [1.5 + 2.0 * k / max(n_nets - 1, 1) for k in range(n_nets)]
+    neurons = [neuron_params(nu_ext_kHz=r) for r in rates]
+    synapses = [synapse_params() for _ in range(n_nets)]
+    seeds = [seed0 + k for k in range(n_nets)]
+    return grids, neurons, synapses, seeds

@@ -1,0 +1,112 @@
+"""The batched form (many independent nets, one persistent launch per call).
+
+Every member must compute exactly what it computes alone: its raster, final
+potentials, calcium and refractory counters equal those of the same net built
+and stepped by itself (whose kernels the parity tests hold to the oracle).
+The grid barrier between the phases waits a bounded number of polls; the
+timeout path is exercised by a barrier that waits for one more block than
+the launch has, which must end the call with SNN_ETIMEOUT.
+"""
+import numpy as np
+import pytest
+
+from paper_1511_09325_gb300 import build as B
+from paper_1511_09325_gb300 import snn
+from paper_1511_09325_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    snn.load()
+
+
+def _key(t, i):
+    return np.sort(np.asarray(t, np.int64) * (1 << 32) + np.asarray(i, np.int64))
+
+
+def _alone(grid, neuron, synapse, seed, prec, steps):
+    with snn.Net(grid[0], grid[1], neuron, synapse, seed, prec) as net:
+        net.set_record_capacity(1 << 22)
+        net.step(steps)
+        t, i, over = net.spikes()
+        assert not over
+        return _key(t, i), net.state()
+
+
+def _check_members(batch, grids, neurons, synapses, seeds, prec, steps):
+    for k, m in enumerate(batch.members):
+        t, i, over = m.spikes()
+        assert not over
+        key, (v, c, r) = _alone(grids[k], neurons[k], synapses[k], seeds[k], prec, steps)
+        assert np.array_equal(_key(t, i), key), k
+        mv, mc, mr = m.state()
+        assert np.array_equal(mv, v) and np.array_equal(mc, c) and np.array_equal(mr, r), k
+        assert m.stats()[2] == steps
+
+
+GRIDS = [(1, 1), (2, 3), (3, 1), (4, 4), (1, 2), (8, 6)]
+
+
+@pytest.mark.parametrize("prec", ["f32w", "f16w"])
+def test_members_match_standalone_runs(prec):
+    n = len(GRIDS)
+    neurons = [W.neuron_params(nu_ext_kHz=1.5 + 2.0 * k / (n - 1)) for k in range(n)]
+    synapses = [W.synapse_params() for _ in range(n)]
+    seeds = [100 + k for k in range(n)]
+    with snn.Batch(GRIDS, neurons, synapses, seeds, prec) as b:
+        for m in b.members:
+            m.set_record_capacity(1 << 22)
+        b.step(1)
+        b.step(99)
+        b.step(200)
+        _check_members(b, GRIDS, neurons, synapses, seeds, prec, 300)
+
+
+def test_mixed_neuron_counts_and_delays():
+    """Members with different column sizes, delay ranges and stencils."""
+    grids = [(2, 2), (3, 2), (1, 1)]
+    neurons = [W.neuron_params(n_per_col=101, n_exc=81, nu_ext_kHz=3.0), W.neuron_params(),
+               W.neuron_params(nu_ext_kHz=2.0)]
+    synapses = [W.synapse_params(k_out=150, d_min=2, d_max=7, stencil_radius=2),
+                W.synapse_params(d_max=32), W.synapse_params(d_min=3, d_max=5)]
+    seeds = [7, 8, 9]
+    with snn.Batch(grids, neurons, synapses, seeds, "f32w") as b:
+        for m in b.members:
+            m.set_record_capacity(1 << 22)
+        b.step(250)
+        _check_members(b, grids, neurons, synapses, seeds, "f32w", 250)
+
+
+def test_tuned_schedule_keeps_results():
+    grids, neurons, synapses, seeds = W.batch_workload(n_nets=8)
+    with snn.Batch(grids, neurons, synapses, seeds, "f32w") as b:
+        for m in b.members:
+            m.set_record_capacity(1 << 22)
+        choice = b.tune(10)  # 2 rounds x 4 schedules x 10 steps
+        assert 0 <= choice < 4
+        b.step(40)
+        _check_members(b, grids, neurons, synapses, seeds, "f32w", 120)
+
+
+def test_member_cannot_be_stepped_alone():
+    with snn.Batch([(1, 1)], [W.neuron_params()], [W.synapse_params()], [1]) as b:
+        h = b.members[0].handle
+        assert snn.load().snn_step(h, 1) == snn.SNN_ESTATE
+
+
+def test_barrier_wait_gives_up_with_timeout():
+    """A barrier that waits for one block too many must return SNN_ETIMEOUT
+    after its bounded polls, and the context stays usable."""
+    with snn.Batch([(2, 2), (1, 1)], [W.neuron_params()] * 2, [W.synapse_params()] * 2,
+                   [3, 4]) as b:
+        b.set_wait(spin_limit=2000, extra_arrivals=1)
+        with pytest.raises(snn.SnnError) as e:
+            b.step(3)
+        assert e.value.code == snn.SNN_ETIMEOUT
+    # the device still works
+    with snn.Net(1, 1, W.neuron_params(), W.synapse_params(), 5, "f32w") as net:
+        net.step(10)
+        assert net.stats()[2] == 10
