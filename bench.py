@@ -37,7 +37,7 @@ def _args():
     ap.add_argument("--workload", default="cols24x24_f32w")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the 96x96 FP16-vs-FP32 comparison")
+                    help="skip the 96x96 FP16-vs-FP32 comparison and the batched form")
     ap.add_argument("--profile-steps", type=int, default=None,
                     help="steps of the per-kernel timing pass (default: all timed steps)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
@@ -302,9 +302,10 @@ def run_ours(args):
     P = K if args.profile_steps is None else min(args.profile_steps, K)
     roofline = _kernel_roofline(snn, torch, cfg, seed, stream, Wm, max(1, P), args.workload)
 
-    extra = None
+    extra = batched = None
     if not args.no_extra and ws == 1:
         extra = _precision_form(snn, torch, stream, Wm)
+        batched = _batched_form(snn, torch, stream)
     cpu = None
     if ws == 1 and not args.no_cpu:
         cb = _cpu_baseline(args.workload)
@@ -337,9 +338,56 @@ def run_ours(args):
         }
         if extra:
             line["precision_form"] = extra
+        if batched:
+            line["batched_form"] = batched
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _batched_form(snn, torch, stream, steps=2000, n_nets=64):
+    """64 independent nets (grids 1x1..8x8, seeds 100-163, external rates
+    1.5-3.5 kHz) advanced by one persistent launch per call, against the same
+    nets stepped one after the other with their own graphs."""
+    grids, neurons, synapses, seeds = W.batch_workload(n_nets)
+    out = {"workload": "batch64", "nets": n_nets, "steps": steps,
+           "neurons": int(sum(g[0] * g[1] for g in grids) * 1240)}
+    t0 = time.perf_counter()
+    b = snn.Batch(grids, neurons, synapses, seeds, "f32w", stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    out["build_s"] = time.perf_counter() - t0
+    out["tuned_choice"] = b.tune(25)
+    tuned_steps = 2 * 4 * 25
+    r0 = sum(m.stats()[0] for m in b.members)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    r1 = sum(m.stats()[0] for m in b.members)
+    b.close()
+    out["events_per_s"] = (r1 - r0) / (ms * 1e-3)
+    out["ms_per_step"] = ms / steps
+    # the same nets, one by one, same steps after the same warm-up
+    total_ms, ev_seq = 0.0, 0.0
+    for g, n, s, sd in zip(grids, neurons, synapses, seeds):
+        net = snn.Net(g[0], g[1], n, s, sd, "f32w", stream=stream.cuda_stream)
+        net.step(tuned_steps)
+        torch.cuda.synchronize()
+        a0 = net.stats()[0]
+        ev0.record(stream)
+        net.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        ev_seq += net.stats()[0] - a0
+        net.close()
+    out["sequential_ms_per_step"] = total_ms / steps
+    out["sequential_events_per_s"] = ev_seq / (total_ms * 1e-3)
+    out["batch_speedup"] = total_ms / ms
+    return out
 
 
 def _precision_form(snn, torch, stream, warmup, steps=1000):

@@ -7,6 +7,7 @@
 // compiled with -ffp-contract=off) so that the results are reproducible.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "snn_internal.h"
 
@@ -74,8 +75,9 @@ int poisson_table(double lam, HostTables* t, std::string* err) {
 }
 
 // Standard-normal quantiles at (m + 0.5) / 65536 by 80 bisection steps on
-// [-8, 8] against Phi(z) = erfc(-z / sqrt(2)) / 2.
-void normal_quantiles(std::vector<double>* q) {
+// [-8, 8] against Phi(z) = erfc(-z / sqrt(2)) / 2.  They depend on no
+// parameter: computed once per process.
+void compute_normal_quantiles(std::vector<double>* q) {
   q->resize(65536);
   for (int m = 0; m < 65536; ++m) {
     const double target = ((double)m + 0.5) / 65536.0;
@@ -90,6 +92,13 @@ void normal_quantiles(std::vector<double>* q) {
     }
     (*q)[m] = 0.5 * (lo + hi);
   }
+}
+
+const std::vector<double>& normal_quantiles() {
+  static std::once_flag once;
+  static std::vector<double> q;
+  std::call_once(once, [] { compute_normal_quantiles(&q); });
+  return q;
 }
 
 // Round a double to binary16, ties to even; returns the 15 magnitude bits
@@ -151,8 +160,7 @@ int make_host_tables(const snn_neuron_params& np, const snn_synapse_params& sp,
 
   // Weights: w = mu (1 + cv Q), clipped to the source population's sign,
   // then stored as float bits (F32W) or half magnitude bits (F16W).
-  std::vector<double> q;
-  normal_quantiles(&q);
+  const std::vector<double>& q = normal_quantiles();
   t->wtab.assign(2 * 65536, 0u);
   const double mus[2] = {(double)sp.w_exc_mV, (double)sp.w_inh_mV};
   for (int p = 0; p < 2; ++p) {
