@@ -32,6 +32,9 @@ struct snn_net {
   int32_t* acc = nullptr;
   uint32_t* ids = nullptr;
   unsigned* cnt = nullptr;
+  unsigned* ccnt = nullptr;
+  unsigned* isum = nullptr;
+  unsigned* gsum = nullptr;
   Ctl* ctl = nullptr;
   unsigned long long* rec = nullptr;
   long long rec_cap = 0;     // requested total record capacity
@@ -133,7 +136,7 @@ void release(snn_net* net) {
   if (net->hhdr) cudaFreeHost(net->hhdr);
   if (net->hstage) cudaFreeHost(net->hstage);
   void* ptrs[] = {net->syn, net->bend, net->V, net->C, net->R, net->acc,
-                  net->ids, net->cnt, net->ctl, net->rec, net->rcnt, net->stage, net->rpre, net->dhdr, net->colcnt,
+                  net->ids, net->cnt, net->ccnt, net->isum, net->gsum, net->ctl, net->rec, net->rcnt, net->stage, net->rpre, net->dhdr, net->colcnt,
                   net->ext_part, net->spk_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -148,6 +151,7 @@ int validate(int gw, int gh, const snn_neuron_params* n, const snn_synapse_param
   };
   if (!n || !s) return bad("null parameter struct");
   if (gw < 1 || gh < 1) return bad("grid must be at least 1x1");
+  if (gw > kMaxGridSide || gh > kMaxGridSide) return bad("grid_w and grid_h must be at most 16383");
   const int nrc = snn::validate_neuron_params(n, why);
   if (nrc != SNN_OK) return nrc;
   if (s->k_out < 1) return bad("k_out must be positive");
@@ -220,6 +224,9 @@ void fill_step_params(snn_net* net) {
   p.acc = net->acc;
   p.ids = net->ids;
   p.cnt = net->cnt;
+  p.ccnt = net->ccnt;
+  p.isum = net->isum;
+  p.gsum = net->gsum;
   p.bend = net->bend;
   p.syn = net->syn;
   p.ctl = net->ctl;
@@ -274,6 +281,9 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if ((rc = dalloc(net, &net->acc, (size_t)net->Npad * 4))) return rc;
   if ((rc = dalloc(net, &net->ids, (size_t)net->nslot * net->N * 4))) return rc;
   if ((rc = dalloc(net, &net->cnt, (size_t)net->nslot * 4))) return rc;
+  if ((rc = dalloc(net, &net->ccnt, (size_t)net->nslot * net->ncol * 4))) return rc;
+  if ((rc = dalloc(net, &net->isum, (size_t)net->ncol * 4))) return rc;
+  if ((rc = dalloc(net, &net->gsum, (size_t)(net->ncol + 31) / 32 * 4))) return rc;
   if ((rc = dalloc(net, &net->ctl, sizeof(Ctl)))) return rc;
   if ((rc = dalloc(net, &net->rec, (size_t)net->rec_region * net->update_grid * 8))) return rc;
   if ((rc = dalloc(net, &net->rcnt, (size_t)net->update_grid * 8))) return rc;
@@ -293,6 +303,11 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if (e == cudaSuccess) e = cudaMemsetAsync(net->ctl, 0, sizeof(Ctl), net->stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(net->cnt, 0, (size_t)net->nslot * 4, net->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(net->ccnt, 0, (size_t)net->nslot * net->ncol * 4, net->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(net->isum, 0, (size_t)net->ncol * 4, net->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(net->gsum, 0, (size_t)(net->ncol + 31) / 32 * 4, net->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(net->colcnt, 0, (size_t)net->ncol * 16, net->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(net->ext_part, 0, (size_t)net->update_grid * 8, net->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(net->spk_part, 0, (size_t)net->update_grid * 8, net->stream);
@@ -734,7 +749,7 @@ struct snn_batch {
   std::vector<snn_net*> nets;
   int precision = 0, num_sms = 0, max_npc = 0;
   int infl = 4;            // 16-byte chunks in flight in the delivery loop
-  int agg = 1;             // per-warp windows
+  int agg = 1;             // block windows for the local half of the synapses
   int choice = -1;         // autotuner's pick (-1: not tuned)
   cudaStream_t stream = nullptr;
   bool own_stream = false;

@@ -17,7 +17,12 @@
 //   R      u8[Npad] remaining refractory steps.
 //   acc    int32[Npad] recurrent input of the next step, 2^-16 mV units.
 //   ids    u32[d_max + 1][N] spike lists of the last d_max + 1 steps (slot
-//          t % (d_max + 1)), cnt[slot] entries each, in neuron-block order.
+//          t % (d_max + 1)); the spikes of column c at step t are
+//          ids[slot][c * n_per_col + r], r < ccnt[slot][c], in no fixed order.
+//   ccnt   u32[d_max + 1][ncol] spikes of each slot's step per column.
+//   isum   u32[ncol] (bucket, spiker) items of each column over the steps that
+//          the next delivery reads (the sum of its d_max - d_min + 1 slots).
+//   gsum   u32[ceil(ncol / 32)] isum summed over groups of 32 columns.
 //   cnt    u32[d_max + 1] spikes of each slot's step.
 //   ctl    control block (step counter, completion counter, overflow flag).
 //   rec    u64 spike records (step << 32 | id), one region per update block,
@@ -47,6 +52,7 @@ constexpr int kMaxPoisThr = 127; // Poisson thresholds below 2^32
 constexpr int kMaxOff = 48;      // remote stencil offsets (radius <= 3)
 constexpr uint32_t kPad = 0xFFFFFFFFu;  // code of a padding record
 constexpr int kCenterCode = (3 << 3) | 3;
+constexpr int kMaxGridSide = 16383;     // columns per grid side (14-bit coordinates)
 
 // Tables computed on the host in FP64 and rounded once.
 struct HostTables {
@@ -82,7 +88,7 @@ struct StepParams {
   long long N;
   int npc, nexc, W, H, K, dmin, ndel, nslot, rowcap;
   int ncol;
-  int agg;  // per-warp shared windows for the local half of the synapses
+  int agg;  // block shared windows for the local half of the synapses
   uint32_t seed_lo, seed_hi;
   float theta, vr, dc, pvv, pcc, pvc_e, pvc_i;
   int32_t jx;
@@ -96,6 +102,9 @@ struct StepParams {
   int32_t* acc;
   uint32_t* ids;
   unsigned* cnt;
+  unsigned* ccnt;  // per-column counts (column-indexed lists); null: one compact list
+  unsigned* isum;  // per-column items of the delivery window (with ccnt)
+  unsigned* gsum;  // isum per group of 32 columns
   const uint8_t* bend;
   const void* syn;
   Ctl* ctl;

@@ -5,30 +5,29 @@
 //   neurons and one Philox4x32-10 block (counter (i/4, t, EXT, 0)) whose 4
 //   words give their external Poisson counts.  It reads and clears their
 //   recurrent input, applies refractoriness, threshold, reset and the exact
-//   propagator with explicitly rounded FP32 operations.  A block buffers the
-//   spikes of a few tiles in shared memory, grouped by column, and appends them
-//   to the step's spike list with one atomic per flush, so neighbouring list
-//   entries come from the same column.  Spike records go to a region of the
-//   record buffer owned by the block; spike and external-event totals to
+//   propagator with explicitly rounded FP32 operations.  A tile's spikes are
+//   counted per column in shared memory and written to their column's part of
+//   the step's spike list (one atomic per column and tile) and to the block's
+//   record region.  The per-column item counts of the next delivery (isum,
+//   gsum) are kept up to date here; spike and external-event totals go to
 //   per-block partial sums.
 //
 // deliver_kernel (event-driven delivery, Sec. 1), "pull by delay": the input
 //   of step t+1 is the sum over delays d of bucket d of every neuron that
 //   spiked at step t+1-d, so only one N-entry accumulator (resident in L2)
 //   receives additions, not a d_max-slot ring.  The (delay bucket, spiker)
-//   items of the last d_max steps form one virtual list, split evenly over a
-//   persistent grid.  A warp takes 32 consecutive items: lane e resolves item
-//   e, then the warp streams the concatenated buckets in 16-byte chunks (4
-//   synapses per lane, four chunks in flight).  The item a chunk belongs to is
-//   found from a ballot over the items' start offsets and the item's fields
-//   travel by shuffle, so the inner loop reads no shared memory.  Each
-//   synapse's weight goes to L2 as a fire-and-forget int32 reduction, except
-//   when all items of the batch come from one column and carry at least
-//   n_per_col / 2 synapse slots: then the
-//   local half (targets in that column) is summed in a per-warp shared-memory
-//   window first and flushed with coalesced reductions.  Integer addition
-//   makes the result independent of the order.  The last block to finish
-//   advances the step counter.
+//   items of the last d_max steps, ordered by (column, bucket, spiker), form
+//   one virtual list split evenly over a persistent grid.  A warp takes 32
+//   consecutive items: lane e resolves item e, then the warp streams the
+//   concatenated buckets in 16-byte chunks (4 synapses per lane, four chunks in
+//   flight).  The item a chunk belongs to is found from a ballot over the
+//   items' start offsets and the item's fields travel by shuffle, so the inner
+//   loop reads no shared memory.  Each synapse's weight goes to L2 as a
+//   fire-and-forget int32 reduction, except that the local half of the
+//   synapses of a block's first columns (targets in the source's own column)
+//   is summed in shared-memory windows and flushed once per block.  Integer
+//   addition makes the result independent of the order.  The last block to
+//   finish advances the step counter.
 #include "snn_device.cuh"
 #include "snn_internal.h"
 
@@ -39,7 +38,6 @@ constexpr int kUpdateThreads = 256;
 constexpr int kDeliverThreads = 256;
 constexpr int kInflight = 4;  // 16-byte synapse chunks in flight per lane
 constexpr int kTile = kUpdateThreads * 4;    // neurons per update tile
-constexpr int kSpikeBuf = 3 * kTile;         // block-local spike buffer
 constexpr int kTileCols = kTile / 2 + 2;     // columns a tile can touch (npc >= 2)
 
 struct NeuronOut {
@@ -92,47 +90,22 @@ __device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
 
 // Shared memory of one update block.
 struct UpdateSmem {
-  uint32_t buf[kSpikeBuf];       // spikes of the tiles since the last flush
   uint32_t thr[kMaxPoisThr + 1];  // Poisson thresholds
   uint8_t guide[256];            // Poisson guide table
   unsigned tpop[kTileCols][2];   // E / I spikes per column of the tile
-  unsigned tpos[kTileCols];      // buffer offset of each column's spikes
-  unsigned fill, base;
+  unsigned tpos[kTileCols];      // first record of each column's spikes in the tile
+  long long lbase[kTileCols];    // list position of each column's first spike
+  long long cbase;               // compact list: position of the tile's first spike
+  unsigned long long rbase;      // record position of the tile's first spike
   unsigned long long rc, spk;
   unsigned ksum[kUpdateThreads / 32];
 };
 
-// Append the block's buffered spikes to the step's list (one atomic) and to
-// the block's own region `vb` of the record buffer (step << 32 | id).
-__device__ __forceinline__ void flush_spikes(const StepParams& P, long long t, int slot, int vb,
-                                             UpdateSmem& S) {
-  const unsigned n = S.fill;  // block-uniform (read after a barrier)
-  if (n == 0u) return;
-  if (threadIdx.x == 0) S.base = atomicAdd(P.cnt + slot, n);
-  __syncthreads();
-  const unsigned base = S.base;
-  const unsigned long long rc = S.rc;
-  uint32_t* list = P.ids + (long long)slot * P.N + base;
-  unsigned long long* region = P.rec + (long long)vb * P.rec_region;
-  for (unsigned e = threadIdx.x; e < n; e += blockDim.x) {
-    const uint32_t id = S.buf[e];
-    list[e] = id;
-    const unsigned long long ri = rc + e;
-    if ((long long)ri < P.rec_region) region[ri] = ((unsigned long long)(unsigned)t << 32) | id;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if ((long long)(rc + n) > P.rec_region) P.ctl->rec_overflow = 1u;
-    S.rc = rc + n;
-    S.spk += n;
-    S.fill = 0u;
-  }
-  __syncthreads();
-}
-
 // Update block vb of vgrid for step t: tiles vb, vb + vgrid, ...  Block vb
 // owns ext_part[vb], spk_part[vb] and record region vb of the net, so the
-// grid size must be the same every step.
+// grid size must be the same every step.  Each spike goes to the step's list
+// (column c's part when P.ccnt is set, else one compact list) and to the
+// block's record region as (step << 32 | id).
 __device__ __forceinline__ void update_body(const StepParams& P, long long t, int vb, int vgrid,
                                             UpdateSmem& S) {
   __syncthreads();  // the shared memory may still be read by a previous body
@@ -140,13 +113,32 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
   for (int m = threadIdx.x; m < 256; m += blockDim.x) S.guide[m] = P.pois_guide[m];
   for (int m = threadIdx.x; m <= kMaxPoisThr; m += blockDim.x) S.thr[m] = P.pois_thr[m];
   if (threadIdx.x == 0) {
-    S.fill = 0u;
     S.rc = P.rcnt[vb];
     S.spk = 0ull;
   }
   unsigned ksum = 0u;
   const long long quads = (P.N + 3) / 4;
   const long long tiles = (quads + kUpdateThreads - 1) / kUpdateThreads;
+  uint32_t* list = P.ids + (long long)slot * P.N;
+  unsigned long long* region = P.rec + (long long)vb * P.rec_region;
+
+  // Move each column's item count (isum, gsum) from the delivery window of
+  // step t - 1, steps t - d_max .. t - d_min, to that of step t: add step
+  // t + 1 - d_min (below, as its spikes are counted, when d_min = 1) and drop
+  // step t - d_max, whose slot is (t + 1) mod (d_max + 1).
+  if (P.ccnt != nullptr) {
+    const long long s_in = t + 1 - P.dmin;
+    const unsigned* in = (P.dmin >= 2 && s_in >= 0) ? P.ccnt + (s_in % P.nslot) * P.ncol : nullptr;
+    const unsigned* out = P.ccnt + ((t + 1) % P.nslot) * P.ncol;
+    for (long long c = (long long)vb * blockDim.x + threadIdx.x; c < P.ncol;
+         c += (long long)vgrid * blockDim.x) {
+      const unsigned d = (in ? in[c] : 0u) - out[c];
+      if (d) {
+        atomicAdd(P.isum + c, d);
+        atomicAdd(P.gsum + (c >> 5), d);
+      }
+    }
+  }
 
   for (long long tile = vb; tile < tiles; tile += vgrid) {
     const long long first = tile * kTile;
@@ -207,24 +199,43 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
                                                       (unsigned char)rout[2], (unsigned char)rout[3]);
     }
     __syncthreads();
-    // place the tile's spikes in the buffer grouped by column (E then I), so
-    // that neighbouring list entries share a column
+    // places: records grouped by column (E then I) in the block's region; list
+    // entries in each column's part of the step's list (or the compact list)
+    if (P.ccnt != nullptr) {
+      for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
+        const unsigned n = S.tpop[k][0] + S.tpop[k][1];
+        const int c = col0 + k;
+        S.lbase[k] = (long long)c * P.npc +
+                     (n ? (long long)atomicAdd(P.ccnt + (long long)slot * P.ncol + c, n) : 0ll);
+        if (n && P.dmin == 1) {
+          atomicAdd(P.isum + c, n);
+          atomicAdd(P.gsum + (c >> 5), n);
+        }
+      }
+    }
     if (threadIdx.x == 0) {
-      unsigned pos = S.fill;
+      unsigned pos = 0u;
       for (int k = 0; k < ncols; ++k) {
         S.tpos[k] = pos;
         pos += S.tpop[k][0] + S.tpop[k][1];
       }
-      S.fill = pos;
+      S.cbase = pos ? (long long)atomicAdd(P.cnt + slot, pos) : 0ll;
+      S.rbase = S.rc;
+      S.rc += pos;
+      S.spk += pos;
     }
     __syncthreads();
+    const unsigned long long rc = S.rbase;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if (scol[e] >= 0) {
         const int k = scol[e];
         const unsigned r = rank[e] & 0x7FFFFFFFu;
         const unsigned off = (rank[e] & 0x80000000u) ? S.tpop[k][0] + r : r;
-        S.buf[S.tpos[k] + off] = (uint32_t)(i0 + e);
+        const uint32_t id = (uint32_t)(i0 + e);
+        list[P.ccnt != nullptr ? S.lbase[k] + off : S.cbase + S.tpos[k] + off] = id;
+        const unsigned long long ri = rc + S.tpos[k] + off;
+        if ((long long)ri < P.rec_region) region[ri] = ((unsigned long long)(unsigned)t << 32) | id;
       }
     }
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
@@ -232,10 +243,7 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
       if (S.tpop[k][1]) atomicAdd(&P.colcnt[2 * (col0 + k) + 1], (unsigned long long)S.tpop[k][1]);
     }
     __syncthreads();
-    if (S.fill > (unsigned)(kSpikeBuf - kTile)) flush_spikes(P, t, slot, vb, S);
   }
-  __syncthreads();
-  flush_spikes(P, t, slot, vb, S);
 
   // external events: per-block partial sum, no atomics
 #pragma unroll
@@ -247,6 +255,7 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
     for (int w = 0; w < kUpdateThreads / 32; ++w) tot += S.ksum[w];
     P.ext_part[vb] += tot;
     P.spk_part[vb] += S.spk;
+    if ((long long)S.rc > P.rec_region) P.ctl->rec_overflow = 1u;
     P.rcnt[vb] = S.rc;
   }
 }
@@ -267,15 +276,23 @@ __device__ __forceinline__ int wrap_near(int v, int n) {
   return wrap(v, n);
 }
 
+constexpr int kWindows = 4;        // shared-memory windows (columns) per delivery block
+constexpr int kTabEntries = 1024;  // (column, bucket) entries per table piece
 constexpr int kDeliverWarps = kDeliverThreads / 32;
 
-// Deliver one synapse record.  win != nullptr: targets in the item's own
-// column go to the warp's shared window instead of L2.
+// Per-item column info travelling with a chunk: cx | cy << 14 | inhibitory
+// source << 28 | (window + 1) << 29, window -1 when the column has none.
+__device__ __forceinline__ uint32_t pack_info(int cx, int cy, bool inh, int widx) {
+  return (uint32_t)cx | ((uint32_t)cy << 14) | ((inh ? 1u : 0u) << 28) | ((uint32_t)(widx + 1) << 29);
+}
+
+// Deliver one synapse record of a spiker whose column info is `info`.
+// Targets in the spiker's own column go to its window when it has one.
 template <int PREC>
-__device__ __forceinline__ void deliver_record(uint32_t code, uint32_t wbits, float wscale,
-                                               uint32_t colxy, int32_t* win,
-                                               const StepParams& P) {
+__device__ __forceinline__ void deliver_record(uint32_t code, uint32_t wbits, uint32_t info,
+                                               int32_t* win_base, const StepParams& P) {
   if (code == kPad) return;
+  const float wscale = (info >> 28) & 1u ? -65536.0f : 65536.0f;
   float w;
   if (PREC == SNN_EXACT_F16W)
     w = __fmul_rn(__half2float(__ushort_as_half((unsigned short)wbits)), wscale);
@@ -284,40 +301,86 @@ __device__ __forceinline__ void deliver_record(uint32_t code, uint32_t wbits, fl
   const int32_t wfx = __float2int_rn(w);
   const int l = (int)(code & 0x7FFu);
   const uint32_t off = (code >> 11) & 63u;
-  if (win != nullptr && off == (uint32_t)kCenterCode) {
-    atomicAdd(win + l, wfx);
+  const int widx = (int)(info >> 29) - 1;
+  if (widx >= 0 && off == (uint32_t)kCenterCode) {
+    atomicAdd(win_base + widx * P.npc + l, wfx);
   } else {
-    const int cx = (int)(colxy & 0xFFFFu), cy = (int)(colxy >> 16);
+    const int cx = (int)(info & 0x3FFFu), cy = (int)((info >> 14) & 0x3FFFu);
     const int ty = wrap_near(cy + (int)(off >> 3) - 3, P.H);
     const int tx = wrap_near(cx + (int)(off & 7u) - 3, P.W);
-    red_add(P.acc + (ty * P.W + tx) * P.npc + l, wfx);
+    red_add(P.acc + ((long long)ty * P.W + tx) * P.npc + l, wfx);
   }
 }
 
-// One warp, one batch of up to 32 consecutive items.
+struct DeliverSmem {
+  unsigned tab[kTabEntries + 1];  // items before each (column, bucket) entry of the piece
+  int slot[kMaxDelays];           // slot of each bucket's step, -1 before step 0
+  unsigned long long wsum[kDeliverWarps];
+  unsigned long long xgp[2];      // items before the group holding lo / hi - 1
+  unsigned long long p0;          // items before column c0
+  int xg[2];                      // group holding lo / hi - 1
+  int c0, c1;                     // first and last column of the block's items
+  unsigned next;                  // next batch of the current piece
+};
+constexpr size_t kDeliverSmemPad = (sizeof(DeliverSmem) + 255) / 256 * 256;
+
+// Block-wide exclusive scan of one 64-bit value per thread; *total gets the
+// sum.  Uses S.wsum; contains two barriers.
+__device__ __forceinline__ unsigned long long block_scan(unsigned long long v, DeliverSmem& S,
+                                                         unsigned long long* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) S.wsum[warp] = incl;
+  __syncthreads();
+  unsigned long long before = 0ull, all = 0ull;
+#pragma unroll
+  for (int w = 0; w < kDeliverWarps; ++w) {
+    const unsigned long long s = S.wsum[w];
+    before += w < warp ? s : 0ull;
+    all += s;
+  }
+  __syncthreads();
+  *total = all;
+  return before + incl - v;
+}
+
+// One warp, one batch of up to 32 items [item, hi) of a table piece whose
+// first column is pc: item k lies in entry e (column pc + e / ndel, bucket
+// e % ndel) with tab[e] <= k < tab[e + 1].
 template <int PREC, int INFL>
 __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item, unsigned hi,
-                                              const unsigned* s_pref, const long long* s_list,
-                                              int32_t* win) {
+                                              const DeliverSmem& S, int n_entries, int pc,
+                                              int32_t* win_base) {
   const int lane = threadIdx.x & 31;
   int len = 0;
   unsigned long long base = 0ull;
-  float ws = 0.f;
-  uint32_t colxy = 0u;
-  int col = -1;
+  uint32_t info = 0u;
   if (item < hi) {
-    int b = 0;
-    while (item >= s_pref[b + 1]) ++b;
-    const uint32_t j = P.ids[s_list[b] + (item - s_pref[b])];
+    int lo_e = 0, hi_e = n_entries;  // tab[lo_e] <= item < tab[hi_e]
+    while (hi_e - lo_e > 1) {
+      const int mid = (lo_e + hi_e) >> 1;
+      if (S.tab[mid] <= item)
+        lo_e = mid;
+      else
+        hi_e = mid;
+    }
+    const int k = lo_e / P.ndel;
+    const int b = lo_e - k * P.ndel;
+    const int c = pc + k;
+    const uint32_t j = P.ids[(long long)S.slot[b] * P.N + (long long)c * P.npc + (item - S.tab[lo_e])];
     const uint8_t* be = P.bend + (long long)j * kBendStride;
     const int beg = (b ? (int)be[b - 1] : 0) * kSlotUnit;
     const int end = (int)be[b] * kSlotUnit;
     len = end - beg;
     base = (unsigned long long)j * (unsigned long long)P.rowcap + (unsigned long long)beg;
-    col = (int)(j / (uint32_t)P.npc);
-    ws = (int)(j - (uint32_t)col * (uint32_t)P.npc) < P.nexc ? 65536.0f : -65536.0f;
-    const int cy = col / P.W;
-    colxy = ((uint32_t)cy << 16) | (uint32_t)(col - cy * P.W);
+    const int cy = c / P.W;
+    const bool inh = (int)(j - (uint32_t)c * (uint32_t)P.npc) >= P.nexc;
+    info = pack_info(c - cy * P.W, cy, inh, (P.agg && k < kWindows) ? k : -1);
   }
   // compact the non-empty items to lanes 0..nit-1
   const unsigned cm = __ballot_sync(0xFFFFFFFFu, len > 0);
@@ -326,9 +389,7 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
   int lenc = __shfl_sync(0xFFFFFFFFu, len, src);
   const unsigned blo0 = __shfl_sync(0xFFFFFFFFu, (unsigned)base, src);
   const unsigned bhi0 = __shfl_sync(0xFFFFFFFFu, (unsigned)(base >> 32), src);
-  const float wsc = __shfl_sync(0xFFFFFFFFu, ws, src);
-  const uint32_t cxy = __shfl_sync(0xFFFFFFFFu, colxy, src);
-  const int colc = __shfl_sync(0xFFFFFFFFu, col, src);
+  const uint32_t infc = __shfl_sync(0xFFFFFFFFu, info, src);
   if (lane >= nit) lenc = 0;
   int incl = lenc;
 #pragma unroll
@@ -342,24 +403,16 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
   const unsigned blo = (unsigned)bc, bhi = (unsigned)(bc >> 32);
   const bool mine = lane < nit;
   const unsigned le_mask = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
-  // one source column and at least n_per_col / 2 synapse slots: sum the
-  // local half in the window (flushing costs one pass over n_per_col entries)
-  const int col0 = __shfl_sync(0xFFFFFFFFu, colc, 0);
-  const bool agg = win != nullptr && 2 * T >= P.npc &&
-                   __all_sync(0xFFFFFFFFu, !mine || colc == col0);
-  int32_t* w = agg ? win : nullptr;
 
   for (int f0 = 0; f0 < T; f0 += 128 * INFL) {
     uint32_t code[INFL][4], wbits[INFL][4];
-    float wsl[INFL];
-    uint32_t cxl[INFL];
+    uint32_t inf[INFL];
     bool in[INFL];
 #pragma unroll
     for (int u = 0; u < INFL; ++u) {
       const int fu = f0 + u * 128;
       in[u] = false;
-      wsl[u] = 0.f;
-      cxl[u] = 0u;
+      inf[u] = 0u;
       if (fu < T) {
         // item of the chunk at flat slot fu + 4 * lane: the item holding fu,
         // plus the items that start between fu and the lane's chunk
@@ -370,8 +423,7 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
         const int e = ebase + __popc(starts & le_mask);
         const unsigned bl = __shfl_sync(0xFFFFFFFFu, blo, e);
         const unsigned bh = __shfl_sync(0xFFFFFFFFu, bhi, e);
-        wsl[u] = __shfl_sync(0xFFFFFFFFu, wsc, e);
-        cxl[u] = __shfl_sync(0xFFFFFFFFu, cxy, e);
+        inf[u] = __shfl_sync(0xFFFFFFFFu, infc, e);
         const int f = fu + 4 * lane;
         in[u] = f < T;
         if (in[u]) {
@@ -401,88 +453,158 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
       if (in[u]) {
 #pragma unroll
         for (int qd = 0; qd < 4; ++qd)
-          deliver_record<PREC>(code[u][qd], wbits[u][qd], wsl[u], cxl[u], w, P);
+          deliver_record<PREC>(code[u][qd], wbits[u][qd], inf[u], win_base, P);
       }
     }
-  }
-  if (agg) {
-    // flush the window with coalesced reductions, leaving it zeroed
-    __syncwarp();
-    int32_t* dst = P.acc + (long long)col0 * P.npc;
-    for (int l = lane; l < P.npc; l += 32) {
-      const int32_t v = win[l];
-      if (v) {
-        red_add(dst + l, v);
-        win[l] = 0;
-      }
-    }
-    __syncwarp();
   }
 }
 
-struct DeliverSmem {
-  unsigned pref[kMaxDelays + 1];  // items per delay bucket, prefix
-  long long list[kMaxDelays];     // list offset per bucket
-  unsigned next;                  // next batch of this block
-};
-constexpr size_t kDeliverSmemPad = (sizeof(DeliverSmem) + 255) / 256 * 256;
-
-// Delivery block vb of vgrid for step t: items [total vb / vgrid, ...) of the
-// (bucket, spiker) list.  win: n_per_col * warps ints of shared memory for the
-// per-warp windows.
+// Delivery block vb of vgrid for step t.  The step's items, ordered by
+// (column, delay bucket, spiker), are split into vgrid equal contiguous
+// ranges; block vb locates the first and last column of its range from the
+// group and column counts (gsum, isum), tabulates the (column, bucket) counts
+// of those columns (in pieces of at most kTabEntries entries) and lets its
+// warps take batches of 32 items.  With P.agg the local targets of the first
+// kWindows columns of each piece are summed in shared memory (win_base,
+// kWindows * n_per_col ints) and flushed once per piece.
 template <int PREC, int INFL>
 __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, int vb, int vgrid,
                                              DeliverSmem& S, int32_t* win_base) {
   __syncthreads();  // the shared memory may still be read by a previous body
-  // the slot that the next update fills holds step t - d_max: no longer read
-  if (vb == 0 && threadIdx.x == 0) P.cnt[(t + 1) % P.nslot] = 0u;
   const int lane = threadIdx.x & 31;
-  int32_t* win = P.agg ? win_base + (threadIdx.x >> 5) * P.npc : nullptr;
-  if (win)
-    for (int l = lane; l < P.npc; l += 32) win[l] = 0;
-  if (threadIdx.x < 32) {
+  const int warp = threadIdx.x >> 5;
+  // the slot that the next update fills holds step t - d_max: no longer read
+  const long long next_slot = (t + 1) % P.nslot;
+  if (vb == 0 && threadIdx.x == 0) P.cnt[next_slot] = 0u;
+  for (long long c = (long long)vb * blockDim.x + threadIdx.x; c < P.ncol;
+       c += (long long)vgrid * blockDim.x)
+    P.ccnt[next_slot * P.ncol + c] = 0u;
+  if (P.agg)
+    for (int l = threadIdx.x; l < kWindows * P.npc; l += blockDim.x) win_base[l] = 0;
+  if (threadIdx.x < kMaxDelays) {
     const int b = threadIdx.x;
-    unsigned n = 0u;
-    long long off = 0;
-    if (b < P.ndel) {
-      const long long s = t + 1 - (P.dmin + b);
-      if (s >= 0) {
-        const long long slot = s % P.nslot;
-        n = P.cnt[slot];
-        off = slot * P.N;
+    const long long s = t + 1 - (P.dmin + b);
+    S.slot[b] = (b < P.ndel && s >= 0) ? (int)(s % P.nslot) : -1;
+  }
+  if (threadIdx.x == 0) {
+    S.c0 = -1;
+    S.c1 = -1;
+    S.next = 0u;
+  }
+
+  // the block's item range, from the group counts
+  const int ngrp = (P.ncol + 31) >> 5;
+  const int per = (ngrp + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int g0 = threadIdx.x * per;
+  unsigned long long mine = 0ull;
+  for (int g = g0; g < g0 + per && g < ngrp; ++g) mine += P.gsum[g];
+  unsigned long long total = 0ull;
+  const unsigned long long excl = block_scan(mine, S, &total);
+  const unsigned long long lo = total * (unsigned long long)vb / (unsigned long long)vgrid;
+  const unsigned long long hi = total * (unsigned long long)(vb + 1) / (unsigned long long)vgrid;
+  if (lo >= hi) return;
+  for (int i = 0; i < 2; ++i) {
+    const unsigned long long x = i == 0 ? lo : hi - 1;
+    if (x >= excl && x < excl + mine) {
+      unsigned long long run = excl;
+      for (int g = g0; g < g0 + per && g < ngrp; ++g) {
+        const unsigned v = P.gsum[g];
+        if (x < run + v) {
+          S.xg[i] = g;
+          S.xgp[i] = run;
+          break;
+        }
+        run += v;
       }
     }
-    unsigned incl = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (b >= o) incl += v;
-    }
-    S.pref[b + 1] = incl;
-    if (b == 0) {
-      S.pref[0] = 0u;
-      S.next = 0u;
-    }
-    S.list[b] = off;
   }
   __syncthreads();
+  // the columns holding lo and hi - 1, from the column counts of their groups
+  if (warp < 2) {
+    const unsigned long long x = warp == 0 ? lo : hi - 1;
+    const int c = S.xg[warp] * 32 + lane;
+    const unsigned v = c < P.ncol ? P.isum[c] : 0u;
+    unsigned incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    const unsigned long long pos = S.xgp[warp] + incl - v;
+    if (c < P.ncol && x >= pos && x < pos + v) {
+      if (warp == 0) {
+        S.c0 = c;
+        S.p0 = pos;
+      } else {
+        S.c1 = c;
+      }
+    }
+  }
+  __syncthreads();
+  const int c0 = S.c0, c1 = S.c1;
+  if (c0 < 0 || c1 < c0) return;  // inconsistent counts: nothing is delivered
 
-  // this block's contiguous share of the step's items, 32 per warp batch
-  const unsigned total = S.pref[P.ndel];
-  const unsigned lo = (unsigned)(((unsigned long long)total * vb) / vgrid);
-  const unsigned hi = (unsigned)(((unsigned long long)total * (vb + 1)) / vgrid);
-  while (true) {
-    unsigned k0 = 0u;
-    if (lane == 0) k0 = atomicAdd(&S.next, 32u);
-    k0 = __shfl_sync(0xFFFFFFFFu, k0, 0);
-    if (lo + k0 >= hi) break;
-    deliver_batch<PREC, INFL>(P, lo + k0 + lane, hi, S.pref, S.list, win);
+  const int cols_per_piece = kTabEntries / P.ndel;
+  unsigned long long pbase = S.p0;  // items before the piece's first column
+  for (int pc = c0; pc <= c1; pc += cols_per_piece) {
+    const int ncp = min(cols_per_piece, c1 - pc + 1);
+    const int n_entries = ncp * P.ndel;
+    // tabulate the piece: 4 consecutive entries per thread
+    unsigned v4[4];
+    unsigned sum4 = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x * 4 + q;
+      unsigned v = 0u;
+      if (e < n_entries) {
+        const int k = e / P.ndel;
+        const int sl = S.slot[e - k * P.ndel];
+        v = sl >= 0 ? P.ccnt[(long long)sl * P.ncol + pc + k] : 0u;
+      }
+      v4[q] = v;
+      sum4 += v;
+    }
+    unsigned long long ptotal = 0ull;
+    unsigned run = (unsigned)block_scan(sum4, S, &ptotal);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x * 4 + q;
+      if (e < n_entries) S.tab[e] = run;
+      run += v4[q];
+    }
+    if (threadIdx.x == 0) S.tab[n_entries] = (unsigned)ptotal;
+    __syncthreads();
+    const unsigned a = lo > pbase ? (unsigned)(lo - pbase) : 0u;
+    const unsigned b = hi > pbase ? (unsigned)min(hi - pbase, ptotal) : 0u;
+    while (a < b) {
+      unsigned k0 = 0u;
+      if (lane == 0) k0 = atomicAdd(&S.next, 32u);
+      k0 = __shfl_sync(0xFFFFFFFFu, k0, 0);
+      if (a + k0 >= b) break;
+      deliver_batch<PREC, INFL>(P, a + k0 + lane, b, S, n_entries, pc, win_base);
+    }
+    __syncthreads();
+    if (P.agg) {
+      // flush the piece's windows with coalesced reductions, leaving them zeroed
+      const int nw = min(kWindows, ncp);
+      for (int m = threadIdx.x; m < nw * P.npc; m += blockDim.x) {
+        const int32_t v = win_base[m];
+        if (v) {
+          const int w = m / P.npc;
+          red_add(P.acc + (long long)(pc + w) * P.npc + (m - w * P.npc), v);
+          win_base[m] = 0;
+        }
+      }
+    }
+    if (threadIdx.x == 0) S.next = 0u;
+    pbase += ptotal;
+    __syncthreads();
   }
 }
 
 template <int PREC>
 __global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepParams P) {
-  extern __shared__ int32_t s_win[];  // [warps][n_per_col] when P.agg
+  extern __shared__ int32_t s_win[];  // [kWindows][n_per_col] when P.agg
   __shared__ DeliverSmem S;
   const long long t = P.ctl->t;
   deliver_body<PREC, kInflight>(P, t, (int)blockIdx.x, (int)gridDim.x, S, s_win);
@@ -697,7 +819,7 @@ cudaError_t launch_update(const StepParams& p, int grid, cudaStream_t st) {
 }
 
 size_t deliver_smem(int npc, bool agg) {
-  return agg ? (size_t)kDeliverWarps * (size_t)npc * sizeof(int32_t) : 0u;
+  return agg ? (size_t)kWindows * (size_t)npc * sizeof(int32_t) : 0u;
 }
 
 // Delivery grid: a persistent grid at full occupancy.
@@ -751,7 +873,7 @@ void* batch_kernel_ptr(int precision, int infl) {
 
 size_t batch_smem(int max_npc) {
   const size_t upd = sizeof(UpdateSmem);
-  const size_t del = kDeliverSmemPad + (size_t)kDeliverWarps * (size_t)max_npc * sizeof(int32_t);
+  const size_t del = kDeliverSmemPad + (size_t)kWindows * (size_t)max_npc * sizeof(int32_t);
   return upd > del ? upd : del;
 }
 
