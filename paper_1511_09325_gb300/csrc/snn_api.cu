@@ -705,10 +705,14 @@ int snn_read_synapses(snn_net* net, int64_t j0, int64_t n, int64_t* target, int3
           w = (int32_t)std::rint(f * 65536.0f);
         }
         if (o >= (long long)n * net->K) return fail(net, SNN_ESTATE, "row holds too many synapses");
-        const int dy = (int)((code >> 14) & 7u) - 3, dx = (int)((code >> 11) & 7u) - 3;
-        const int ty = ((cy + dy) % net->H + net->H) % net->H;
-        const int tx = ((cx + dx) % net->W + net->W) % net->W;
-        target[o] = ((long long)ty * net->W + tx) * net->npc + (code & 0x7FFu);
+        if (net->precision == SNN_EXACT_F16W) {
+          const int dy = (int)((code >> 14) & 7u) - 3, dx = (int)((code >> 11) & 7u) - 3;
+          const int ty = ((cy + dy) % net->H + net->H) % net->H;
+          const int tx = ((cx + dx) % net->W + net->W) % net->W;
+          target[o] = ((long long)ty * net->W + tx) * net->npc + (code & 0x7FFu);
+        } else {
+          target[o] = (long long)code;
+        }
         delay[o] = net->dmin + b;
         wfx[o] = w;
         ++o;

@@ -7,6 +7,8 @@
 //   k >= k_local : stencil offset = first m with x1 < thr[m] (P ~ exp(-r/lambda)),
 //                  target l = u_n(x0) in column ((x+dx) mod W, (y+dy) mod H);
 //   delay d = d_min + u_ndel(x2);  weight = table[population][x3 >> 16].
+// F16W records keep the target as a stencil code, F32W records as the target's
+// neuron index.
 // One warp owns one row: a first pass counts the synapses of every delay
 // bucket, a second pass regenerates them and stores each into its bucket in
 // k order (warp match + popc rank), then the bucket tails are padded.
@@ -25,9 +27,12 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
   __shared__ unsigned s_cur[kBuildWarps][32];
   __shared__ uint32_t s_thr[kMaxOff];
   __shared__ int s_code[kMaxOff];
+  __shared__ int s_dx[kMaxOff], s_dy[kMaxOff];
   for (int m = threadIdx.x; m < kMaxOff; m += blockDim.x) {
     s_thr[m] = P.stencil_thr[m];
     s_code[m] = m < P.n_off ? ((P.off_dy[m] + 3) << 3) | (P.off_dx[m] + 3) : kCenterCode;
+    s_dx[m] = m < P.n_off ? P.off_dx[m] : 0;
+    s_dy[m] = m < P.n_off ? P.off_dy[m] : 0;
   }
   __syncthreads();
   const int w = threadIdx.x >> 5;
@@ -66,15 +71,24 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
       const bool valid = k < P.K;
       const uint4 x = philox4x32_10(make_uint4(jj, (uint32_t)k, kTagConn, 0u), P.seed_lo, P.seed_hi);
       const int b = valid ? (int)below(x.z, ndel) : 63;
-      uint32_t code;
+      uint32_t code;  // F16W: stencil code; F32W: target neuron index
       if (k < P.k_local) {
         uint32_t l = below(x.x, (uint32_t)(P.npc - 1));
         l += (l >= (uint32_t)lj) ? 1u : 0u;
-        code = ((uint32_t)kCenterCode << 11) | l;
+        code = PREC == SNN_EXACT_F16W ? ((uint32_t)kCenterCode << 11) | l
+                                      : (uint32_t)col * (uint32_t)P.npc + l;
       } else {
         int m = 0;
         for (int i = 0; i + 1 < P.n_off; ++i) m += (x.y >= s_thr[i]) ? 1 : 0;
-        code = ((uint32_t)s_code[m] << 11) | below(x.x, (uint32_t)P.npc);
+        const uint32_t l = below(x.x, (uint32_t)P.npc);
+        if (PREC == SNN_EXACT_F16W) {
+          code = ((uint32_t)s_code[m] << 11) | l;
+        } else {
+          const int cy = col / P.W, cx = col - cy * P.W;
+          const int ty = wrap(cy + s_dy[m], P.H);
+          const int tx = wrap(cx + s_dx[m], P.W);
+          code = ((uint32_t)ty * (uint32_t)P.W + (uint32_t)tx) * (uint32_t)P.npc + l;
+        }
       }
       const uint32_t wbits = wt[x.w >> 16];
       const unsigned peers = __match_any_sync(0xFFFFFFFFu, b);

@@ -23,11 +23,11 @@
 //   flight).  The item a chunk belongs to is found from a ballot over the
 //   items' start offsets and the item's fields travel by shuffle, so the inner
 //   loop reads no shared memory.  Each synapse's weight goes to L2 as a
-//   fire-and-forget int32 reduction, except that the local half of the
-//   synapses of a block's first columns (targets in the source's own column)
-//   is summed in shared-memory windows and flushed once per block.  Integer
-//   addition makes the result independent of the order.  The last block to
-//   finish advances the step counter.
+//   fire-and-forget int32 reduction, except that synapses onto the first
+//   columns of a block's range (where its spikers sit, so about half of their
+//   synapses) are summed in shared-memory windows and flushed once per block.
+//   Integer addition makes the result independent of the order.  The last
+//   block to finish advances the step counter.
 #include "snn_device.cuh"
 #include "snn_internal.h"
 
@@ -79,11 +79,16 @@ __device__ __forceinline__ int poisson_count(uint32_t x, const uint8_t* guide,
   return k;
 }
 
-// Fire-and-forget int32 reduction into the accumulator, with an L2
-// evict-last hint: the accumulator is re-read by the next step's update.
-__device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
+// L2 evict-last policy for the accumulator, which the next step's update
+// re-reads.
+__device__ __forceinline__ uint64_t evict_last_policy() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// Fire-and-forget int32 reduction into the accumulator under policy `pol`.
+__device__ __forceinline__ void red_add(int32_t* p, int32_t v, uint64_t pol) {
   asm volatile("red.global.add.L2::cache_hint.s32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol)
                : "memory");
 }
@@ -122,23 +127,15 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
   uint32_t* list = P.ids + (long long)slot * P.N;
   unsigned long long* region = P.rec + (long long)vb * P.rec_region;
 
-  // Move each column's item count (isum, gsum) from the delivery window of
-  // step t - 1, steps t - d_max .. t - d_min, to that of step t: add step
-  // t + 1 - d_min (below, as its spikes are counted, when d_min = 1) and drop
-  // step t - d_max, whose slot is (t + 1) mod (d_max + 1).
-  if (P.ccnt != nullptr) {
-    const long long s_in = t + 1 - P.dmin;
-    const unsigned* in = (P.dmin >= 2 && s_in >= 0) ? P.ccnt + (s_in % P.nslot) * P.ncol : nullptr;
-    const unsigned* out = P.ccnt + ((t + 1) % P.nslot) * P.ncol;
-    for (long long c = (long long)vb * blockDim.x + threadIdx.x; c < P.ncol;
-         c += (long long)vgrid * blockDim.x) {
-      const unsigned d = (in ? in[c] : 0u) - out[c];
-      if (d) {
-        atomicAdd(P.isum + c, d);
-        atomicAdd(P.gsum + (c >> 5), d);
-      }
-    }
-  }
+  // Each column's item count (isum, gsum) moves from the delivery window of
+  // step t - 1, steps t - d_max .. t - d_min, to that of step t: step
+  // t + 1 - d_min comes in (as its spikes are counted, when d_min = 1) and
+  // step t - d_max, whose slot is (t + 1) mod (d_max + 1), goes out.  The tile
+  // in which a column starts applies the change for that column.
+  const long long s_in = t + 1 - P.dmin;
+  const unsigned* cin_ = (P.ccnt != nullptr && P.dmin >= 2 && s_in >= 0)
+                             ? P.ccnt + (s_in % P.nslot) * P.ncol : nullptr;
+  const unsigned* cout_ = P.ccnt != nullptr ? P.ccnt + ((t + 1) % P.nslot) * P.ncol : nullptr;
 
   for (long long tile = vb; tile < tiles; tile += vgrid) {
     const long long first = tile * kTile;
@@ -207,9 +204,11 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
         const int c = col0 + k;
         S.lbase[k] = (long long)c * P.npc +
                      (n ? (long long)atomicAdd(P.ccnt + (long long)slot * P.ncol + c, n) : 0ll);
-        if (n && P.dmin == 1) {
-          atomicAdd(P.isum + c, n);
-          atomicAdd(P.gsum + (c >> 5), n);
+        unsigned d = P.dmin == 1 ? n : 0u;
+        if ((long long)c * P.npc >= first) d += (cin_ ? cin_[c] : 0u) - cout_[c];
+        if (d) {
+          atomicAdd(P.isum + c, d);
+          atomicAdd(P.gsum + (c >> 5), d);
         }
       }
     }
@@ -260,7 +259,7 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
   }
 }
 
-__global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams P) {
+__global__ void __launch_bounds__(kUpdateThreads, 5) update_kernel(const StepParams P) {
   __shared__ UpdateSmem S;
   update_body(P, P.ctl->t, (int)blockIdx.x, (int)gridDim.x, S);
 }
@@ -280,36 +279,40 @@ constexpr int kWindows = 4;        // shared-memory windows (columns) per delive
 constexpr int kTabEntries = 1024;  // (column, bucket) entries per table piece
 constexpr int kDeliverWarps = kDeliverThreads / 32;
 
-// Per-item column info travelling with a chunk: cx | cy << 14 | inhibitory
-// source << 28 | (window + 1) << 29, window -1 when the column has none.
-__device__ __forceinline__ uint32_t pack_info(int cx, int cy, bool inh, int widx) {
-  return (uint32_t)cx | ((uint32_t)cy << 14) | ((inh ? 1u : 0u) << 28) | ((uint32_t)(widx + 1) << 29);
+// Per-item info travelling with a chunk: the spiker's column cx | cy << 14
+// and whether it is inhibitory (bit 28).
+__device__ __forceinline__ uint32_t pack_info(int cx, int cy, bool inh) {
+  return (uint32_t)cx | ((uint32_t)cy << 14) | ((inh ? 1u : 0u) << 28);
 }
 
 // Deliver one synapse record of a spiker whose column info is `info`.
-// Targets in the spiker's own column go to its window when it has one.
+// Targets in neurons wbase .. wbase + wlen - 1 (the block's window columns)
+// are summed in the shared windows win, the others reduced into L2.
 template <int PREC>
 __device__ __forceinline__ void deliver_record(uint32_t code, uint32_t wbits, uint32_t info,
-                                               int32_t* win_base, const StepParams& P) {
+                                               int32_t* win, uint32_t wbase, uint32_t wlen,
+                                               uint64_t pol, const StepParams& P) {
   if (code == kPad) return;
-  const float wscale = (info >> 28) & 1u ? -65536.0f : 65536.0f;
   float w;
-  if (PREC == SNN_EXACT_F16W)
+  uint32_t target;
+  if (PREC == SNN_EXACT_F16W) {
+    const float wscale = (info >> 28) & 1u ? -65536.0f : 65536.0f;
     w = __fmul_rn(__half2float(__ushort_as_half((unsigned short)wbits)), wscale);
-  else
-    w = __fmul_rn(__uint_as_float(wbits), 65536.0f);
-  const int32_t wfx = __float2int_rn(w);
-  const int l = (int)(code & 0x7FFu);
-  const uint32_t off = (code >> 11) & 63u;
-  const int widx = (int)(info >> 29) - 1;
-  if (widx >= 0 && off == (uint32_t)kCenterCode) {
-    atomicAdd(win_base + widx * P.npc + l, wfx);
-  } else {
+    const uint32_t off = (code >> 11) & 63u;
     const int cx = (int)(info & 0x3FFFu), cy = (int)((info >> 14) & 0x3FFFu);
     const int ty = wrap_near(cy + (int)(off >> 3) - 3, P.H);
     const int tx = wrap_near(cx + (int)(off & 7u) - 3, P.W);
-    red_add(P.acc + ((long long)ty * P.W + tx) * P.npc + l, wfx);
+    target = ((uint32_t)ty * (uint32_t)P.W + (uint32_t)tx) * (uint32_t)P.npc + (code & 0x7FFu);
+  } else {
+    w = __fmul_rn(__uint_as_float(wbits), 65536.0f);
+    target = code;
   }
+  const int32_t wfx = __float2int_rn(w);
+  const uint32_t rel = target - wbase;
+  if (rel < wlen)
+    atomicAdd(win + rel, wfx);
+  else
+    red_add(P.acc + target, wfx, pol);
 }
 
 struct DeliverSmem {
@@ -355,7 +358,8 @@ __device__ __forceinline__ unsigned long long block_scan(unsigned long long v, D
 template <int PREC, int INFL>
 __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item, unsigned hi,
                                               const DeliverSmem& S, int n_entries, int pc,
-                                              int32_t* win_base) {
+                                              int32_t* win, uint32_t wbase, uint32_t wlen,
+                                              uint64_t pol) {
   const int lane = threadIdx.x & 31;
   int len = 0;
   unsigned long long base = 0ull;
@@ -380,7 +384,7 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
     base = (unsigned long long)j * (unsigned long long)P.rowcap + (unsigned long long)beg;
     const int cy = c / P.W;
     const bool inh = (int)(j - (uint32_t)c * (uint32_t)P.npc) >= P.nexc;
-    info = pack_info(c - cy * P.W, cy, inh, (P.agg && k < kWindows) ? k : -1);
+    info = pack_info(c - cy * P.W, cy, inh);
   }
   // compact the non-empty items to lanes 0..nit-1
   const unsigned cm = __ballot_sync(0xFFFFFFFFu, len > 0);
@@ -453,7 +457,7 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
       if (in[u]) {
 #pragma unroll
         for (int qd = 0; qd < 4; ++qd)
-          deliver_record<PREC>(code[u][qd], wbits[u][qd], inf[u], win_base, P);
+          deliver_record<PREC>(code[u][qd], wbits[u][qd], inf[u], win, wbase, wlen, pol, P);
       }
     }
   }
@@ -464,9 +468,10 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
 // ranges; block vb locates the first and last column of its range from the
 // group and column counts (gsum, isum), tabulates the (column, bucket) counts
 // of those columns (in pieces of at most kTabEntries entries) and lets its
-// warps take batches of 32 items.  With P.agg the local targets of the first
-// kWindows columns of each piece are summed in shared memory (win_base,
-// kWindows * n_per_col ints) and flushed once per piece.
+// warps take batches of 32 items.  With P.agg the synapses onto the first
+// kWindows columns of each piece, from any of the piece's items, are summed
+// in shared memory (win_base, kWindows * n_per_col ints) and flushed once per
+// piece.
 template <int PREC, int INFL>
 __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, int vb, int vgrid,
                                              DeliverSmem& S, int32_t* win_base) {
@@ -544,6 +549,7 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
   const int c0 = S.c0, c1 = S.c1;
   if (c0 < 0 || c1 < c0) return;  // inconsistent counts: nothing is delivered
 
+  const uint64_t pol = evict_last_policy();
   const int cols_per_piece = kTabEntries / P.ndel;
   unsigned long long pbase = S.p0;  // items before the piece's first column
   for (int pc = c0; pc <= c1; pc += cols_per_piece) {
@@ -576,24 +582,23 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
     __syncthreads();
     const unsigned a = lo > pbase ? (unsigned)(lo - pbase) : 0u;
     const unsigned b = hi > pbase ? (unsigned)min(hi - pbase, ptotal) : 0u;
+    // windows: the piece's first columns, for synapses from any of its items
+    const uint32_t wbase = (uint32_t)pc * (uint32_t)P.npc;
+    const uint32_t wlen = P.agg ? (uint32_t)min(kWindows, ncp) * (uint32_t)P.npc : 0u;
     while (a < b) {
       unsigned k0 = 0u;
       if (lane == 0) k0 = atomicAdd(&S.next, 32u);
       k0 = __shfl_sync(0xFFFFFFFFu, k0, 0);
       if (a + k0 >= b) break;
-      deliver_batch<PREC, INFL>(P, a + k0 + lane, b, S, n_entries, pc, win_base);
+      deliver_batch<PREC, INFL>(P, a + k0 + lane, b, S, n_entries, pc, win_base, wbase, wlen, pol);
     }
     __syncthreads();
-    if (P.agg) {
-      // flush the piece's windows with coalesced reductions, leaving them zeroed
-      const int nw = min(kWindows, ncp);
-      for (int m = threadIdx.x; m < nw * P.npc; m += blockDim.x) {
-        const int32_t v = win_base[m];
-        if (v) {
-          const int w = m / P.npc;
-          red_add(P.acc + (long long)(pc + w) * P.npc + (m - w * P.npc), v);
-          win_base[m] = 0;
-        }
+    // flush the windows with coalesced reductions, leaving them zeroed
+    for (uint32_t m = threadIdx.x; m < wlen; m += blockDim.x) {
+      const int32_t v = win_base[m];
+      if (v) {
+        red_add(P.acc + wbase + m, v, pol);
+        win_base[m] = 0;
       }
     }
     if (threadIdx.x == 0) S.next = 0u;
