@@ -85,7 +85,7 @@ enum {
 
 /* Weight storage of the outgoing-synapse table. */
 enum {
-  SNN_EXACT_F32W = 0, /* 8 B/synapse: target neuron index + FP32 weight     */
+  SNN_EXACT_F32W = 0, /* 8 B/synapse: target index + FP32 weight (2^-16 mV) */
   SNN_EXACT_F16W = 1  /* 4 B/synapse: packed target + FP16 weight magnitude  */
 };
 

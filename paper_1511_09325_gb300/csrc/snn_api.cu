@@ -700,9 +700,7 @@ int snn_read_synapses(snn_net* net, int64_t j0, int64_t n, int64_t* target, int3
           std::memcpy(&code, rp, 4);
           std::memcpy(&wbits, rp + 4, 4);
           if (code == kPad) continue;
-          float f;
-          std::memcpy(&f, &wbits, 4);
-          w = (int32_t)std::rint(f * 65536.0f);
+          w = (int32_t)wbits;
         }
         if (o >= (long long)n * net->K) return fail(net, SNN_ESTATE, "row holds too many synapses");
         if (net->precision == SNN_EXACT_F16W) {

@@ -7,8 +7,9 @@
 //   k >= k_local : stencil offset = first m with x1 < thr[m] (P ~ exp(-r/lambda)),
 //                  target l = u_n(x0) in column ((x+dx) mod W, (y+dy) mod H);
 //   delay d = d_min + u_ndel(x2);  weight = table[population][x3 >> 16].
-// F16W records keep the target as a stencil code, F32W records as the target's
-// neuron index.
+// F16W records keep the target as a stencil code and the weight's magnitude as
+// a half; F32W records keep the target's neuron index and the FP32 weight
+// already scaled to the input's fixed-point units, round(w * 2^16).
 // One warp owns one row: a first pass counts the synapses of every delay
 // bucket, a second pass regenerates them and stores each into its bucket in
 // k order (warp match + popc rank), then the bucket tails are padded.
@@ -96,10 +97,13 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
       const unsigned pos = s_cur[w][b & 31] + rank;
       __syncwarp();
       if (valid) {
-        if (PREC == SNN_EXACT_F16W)
+        if (PREC == SNN_EXACT_F16W) {
           static_cast<uint32_t*>(P.syn)[row + pos] = ((wbits & 0x7FFFu) << 17) | code;
-        else
-          static_cast<uint2*>(P.syn)[row + pos] = make_uint2(code, wbits);
+        } else {
+          // the FP32 weight, delivered as round(w * 2^16) in the input's units
+          const int32_t wfx = __float2int_rn(__fmul_rn(__uint_as_float(wbits), 65536.0f));
+          static_cast<uint2*>(P.syn)[row + pos] = make_uint2(code, (uint32_t)wfx);
+        }
         if (rank == 0) s_cur[w][b] += __popc(peers);
       }
       __syncwarp();

@@ -7,7 +7,8 @@
 //          records up to the next multiple of 8 (so a bucket is a whole number
 //          of 32 B sectors in the F16W layout).
 //            F16W: u32 record  = half_magnitude(15) << 17 | code(17)
-//            F32W: u32x2 record = { target neuron index, float weight bits }
+//            F32W: u32x2 record = { target neuron index, int32 round(w * 2^16) }
+//          (w the FP32 weight in mV, so the record holds exactly what is added)
 //          code = ((dy + 3) << 3 | (dx + 3)) << 11 | l  (stencil offset of the
 //          target column and index l inside it; local synapses use dx=dy=0).
 //          The weight's sign is the source population's (Dale's principle),

@@ -93,6 +93,25 @@ __device__ __forceinline__ void red_add(int32_t* p, int32_t v, uint64_t pol) {
                : "memory");
 }
 
+// The same, issued only where `on` is nonzero: a predicated instruction, so
+// lanes that take different paths do not split the warp.
+__device__ __forceinline__ void red_add_if(uint32_t on, int32_t* p, int32_t v, uint64_t pol) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+      "@q red.global.add.L2::cache_hint.s32 [%1], %2, %3;\n\t}" ::"r"(on),
+      "l"(p), "r"(v), "l"(pol)
+      : "memory");
+}
+
+// Predicated int32 reduction into shared memory (shared-window address `a`).
+__device__ __forceinline__ void red_shared_if(uint32_t on, uint32_t a, int32_t v) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+      "@q red.shared.add.s32 [%1], %2;\n\t}" ::"r"(on),
+      "r"(a), "r"(v)
+      : "memory");
+}
+
 // Shared memory of one update block.
 struct UpdateSmem {
   uint32_t thr[kMaxPoisThr + 1];  // Poisson thresholds
@@ -287,32 +306,32 @@ __device__ __forceinline__ uint32_t pack_info(int cx, int cy, bool inh) {
 
 // Deliver one synapse record of a spiker whose column info is `info`.
 // Targets in neurons wbase .. wbase + wlen - 1 (the block's window columns)
-// are summed in the shared windows win, the others reduced into L2.
+// are summed in the shared windows at shared address win_s, the others
+// reduced into L2.  Padding records deliver nothing.  Both reductions are
+// predicated, so the warp never diverges here.
 template <int PREC>
 __device__ __forceinline__ void deliver_record(uint32_t code, uint32_t wbits, uint32_t info,
-                                               int32_t* win, uint32_t wbase, uint32_t wlen,
+                                               uint32_t win_s, uint32_t wbase, uint32_t wlen,
                                                uint64_t pol, const StepParams& P) {
-  if (code == kPad) return;
-  float w;
+  const bool valid = code != kPad;
   uint32_t target;
+  int32_t wfx;
   if (PREC == SNN_EXACT_F16W) {
     const float wscale = (info >> 28) & 1u ? -65536.0f : 65536.0f;
-    w = __fmul_rn(__half2float(__ushort_as_half((unsigned short)wbits)), wscale);
+    wfx = __float2int_rn(__fmul_rn(__half2float(__ushort_as_half((unsigned short)wbits)), wscale));
     const uint32_t off = (code >> 11) & 63u;
     const int cx = (int)(info & 0x3FFFu), cy = (int)((info >> 14) & 0x3FFFu);
     const int ty = wrap_near(cy + (int)(off >> 3) - 3, P.H);
     const int tx = wrap_near(cx + (int)(off & 7u) - 3, P.W);
     target = ((uint32_t)ty * (uint32_t)P.W + (uint32_t)tx) * (uint32_t)P.npc + (code & 0x7FFu);
   } else {
-    w = __fmul_rn(__uint_as_float(wbits), 65536.0f);
+    wfx = (int32_t)wbits;
     target = code;
   }
-  const int32_t wfx = __float2int_rn(w);
   const uint32_t rel = target - wbase;
-  if (rel < wlen)
-    atomicAdd(win + rel, wfx);
-  else
-    red_add(P.acc + target, wfx, pol);
+  const bool inwin = rel < wlen;
+  red_shared_if(valid && inwin, win_s + 4u * rel, wfx);
+  red_add_if(valid && !inwin, P.acc + (valid ? target : 0u), wfx, pol);
 }
 
 struct DeliverSmem {
@@ -358,7 +377,7 @@ __device__ __forceinline__ unsigned long long block_scan(unsigned long long v, D
 template <int PREC, int INFL>
 __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item, unsigned hi,
                                               const DeliverSmem& S, int n_entries, int pc,
-                                              int32_t* win, uint32_t wbase, uint32_t wlen,
+                                              uint32_t win_s, uint32_t wbase, uint32_t wlen,
                                               uint64_t pol) {
   const int lane = threadIdx.x & 31;
   int len = 0;
@@ -417,6 +436,11 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
       const int fu = f0 + u * 128;
       in[u] = false;
       inf[u] = 0u;
+#pragma unroll
+      for (int qd = 0; qd < 4; ++qd) {
+        code[u][qd] = kPad;
+        wbits[u][qd] = 0u;
+      }
       if (fu < T) {
         // item of the chunk at flat slot fu + 4 * lane: the item holding fu,
         // plus the items that start between fu and the lane's chunk
@@ -454,11 +478,10 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
     }
 #pragma unroll
     for (int u = 0; u < INFL; ++u) {
-      if (in[u]) {
 #pragma unroll
-        for (int qd = 0; qd < 4; ++qd)
-          deliver_record<PREC>(code[u][qd], wbits[u][qd], inf[u], win, wbase, wlen, pol, P);
-      }
+      for (int qd = 0; qd < 4; ++qd)
+        deliver_record<PREC>(in[u] ? code[u][qd] : kPad, wbits[u][qd], inf[u], win_s, wbase, wlen,
+                             pol, P);
     }
   }
 }
@@ -550,6 +573,7 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
   if (c0 < 0 || c1 < c0) return;  // inconsistent counts: nothing is delivered
 
   const uint64_t pol = evict_last_policy();
+  const uint32_t win_s = (uint32_t)__cvta_generic_to_shared(win_base);
   const int cols_per_piece = kTabEntries / P.ndel;
   unsigned long long pbase = S.p0;  // items before the piece's first column
   for (int pc = c0; pc <= c1; pc += cols_per_piece) {
@@ -590,7 +614,7 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
       if (lane == 0) k0 = atomicAdd(&S.next, 32u);
       k0 = __shfl_sync(0xFFFFFFFFu, k0, 0);
       if (a + k0 >= b) break;
-      deliver_batch<PREC, INFL>(P, a + k0 + lane, b, S, n_entries, pc, win_base, wbase, wlen, pol);
+      deliver_batch<PREC, INFL>(P, a + k0 + lane, b, S, n_entries, pc, win_s, wbase, wlen, pol);
     }
     __syncthreads();
     // flush the windows with coalesced reductions, leaving them zeroed
