@@ -43,8 +43,12 @@ struct snn_net {
   unsigned long long* stage = nullptr;   // drained records, contiguous
   unsigned long long* rpre = nullptr;    // records kept before each region
   unsigned long long* dhdr = nullptr;    // drain header (device)
-  unsigned long long* hhdr = nullptr;    // drain header (pinned host)
-  unsigned long long* hstage = nullptr;  // drained records (pinned host)
+  unsigned long long* hhdr = nullptr;    // drain header (pinned, mapped)
+  unsigned long long* hhdr_dev = nullptr;
+  unsigned long long* hmap = nullptr;    // drained records, small drains (pinned, mapped)
+  unsigned long long* hmap_dev = nullptr;
+  long long hmap_cap = 0;
+  unsigned long long* hstage = nullptr;  // drained records, large drains (pinned host)
   long long hstage_cap = 0;
   unsigned long long* colcnt = nullptr;
   unsigned long long* ext_part = nullptr;
@@ -134,6 +138,7 @@ void free_graphs(snn_net* net) {
 void release(snn_net* net) {
   free_graphs(net);
   if (net->hhdr) cudaFreeHost(net->hhdr);
+  if (net->hmap) cudaFreeHost(net->hmap);
   if (net->hstage) cudaFreeHost(net->hstage);
   void* ptrs[] = {net->syn, net->bend, net->V, net->C, net->R, net->acc,
                   net->ids, net->cnt, net->ccnt, net->isum, net->gsum, net->ctl, net->rec, net->rcnt, net->stage, net->rpre, net->dhdr, net->colcnt,
@@ -290,7 +295,11 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if ((rc = dalloc(net, &net->stage, (size_t)net->rec_region * net->update_grid * 8))) return rc;
   if ((rc = dalloc(net, &net->dhdr, 16))) return rc;
   if ((rc = dalloc(net, &net->rpre, (size_t)net->update_grid * 8))) return rc;
-  SNN_CUDA(net, cudaMallocHost(&net->hhdr, 16));
+  SNN_CUDA(net, cudaHostAlloc(&net->hhdr, 16, cudaHostAllocMapped));
+  SNN_CUDA(net, cudaHostGetDevicePointer(&net->hhdr_dev, net->hhdr, 0));
+  net->hmap_cap = std::min<long long>(net->rec_region * net->update_grid, kMappedRecords);
+  SNN_CUDA(net, cudaHostAlloc(&net->hmap, (size_t)net->hmap_cap * 8, cudaHostAllocMapped));
+  SNN_CUDA(net, cudaHostGetDevicePointer(&net->hmap_dev, net->hmap, 0));
   if ((rc = dalloc(net, &net->colcnt, (size_t)net->ncol * 2 * 8))) return rc;
   if ((rc = dalloc(net, &net->ext_part, (size_t)net->update_grid * 8))) return rc;
   if ((rc = dalloc(net, &net->spk_part, (size_t)net->update_grid * 8))) return rc;
@@ -515,15 +524,18 @@ int snn_read_spikes(snn_net* net, int32_t* steps, int32_t* ids, int64_t cap, int
   if (!net || !n_out || cap < 0 || (cap > 0 && (!steps || !ids)))
     return fail(net, SNN_EINVAL, "bad argument");
   *n_out = 0;
-  // compact the regions on the device and reset them, then two copies
+  // compact the regions on the device and reset them; a drain of at most
+  // hmap_cap records lands in mapped host memory directly, a larger one is
+  // copied from the device stage afterwards
   SNN_CUDA(net, launch_drain_records(net->sp, net->update_grid, net->rpre, net->stage,
-                                     net->dhdr, net->stream));
-  SNN_CUDA(net, cudaMemcpyAsync(net->hhdr, net->dhdr, 16, cudaMemcpyDeviceToHost, net->stream));
+                                     net->dhdr, net->hhdr_dev, net->hmap_dev, net->hmap_cap,
+                                     net->stream));
   SNN_CUDA(net, cudaStreamSynchronize(net->stream));
   const long long kept = (long long)net->hhdr[0];
   bool lost = net->hhdr[1] != 0ull || kept > cap;
   const long long n = kept < cap ? kept : cap;
-  if (n > 0) {
+  const unsigned long long* h = net->hmap;
+  if (n > 0 && kept > net->hmap_cap) {
     if (n > net->hstage_cap) {
       if (net->hstage) cudaFreeHost(net->hstage);
       net->hstage = nullptr;
@@ -535,9 +547,11 @@ int snn_read_spikes(snn_net* net, int32_t* steps, int32_t* ids, int64_t cap, int
     SNN_CUDA(net, cudaMemcpyAsync(net->hstage, net->stage, (size_t)n * 8, cudaMemcpyDeviceToHost,
                                   net->stream));
     SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+    h = net->hstage;
+  }
+  if (n > 0) {
     // each region is in step order: a counting sort by step puts the window
     // in step order (within a step the order stays unspecified)
-    const unsigned long long* h = net->hstage;
     uint32_t tmin = 0xFFFFFFFFu, tmax = 0u;
     for (long long k = 0; k < n; ++k) {
       const uint32_t t = (uint32_t)(h[k] >> 32);

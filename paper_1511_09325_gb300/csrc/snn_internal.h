@@ -153,11 +153,15 @@ cudaError_t launch_update(const StepParams& p, int grid, cudaStream_t st);
 int update_grid(long long N, int num_sms);
 cudaError_t launch_deliver(const StepParams& p, int precision, int grid, cudaStream_t st);
 int deliver_grid(int precision, int num_sms, int npc, bool agg);
-// Compact the per-block record regions into stage and reset them; header[0] =
-// records kept, header[1] = 1 if records were dropped.
+// Compact the per-block record regions and reset them; header[0] = records
+// kept, header[1] = 1 if records were dropped (written to header and to the
+// mapped host header map_hdr).  The records go to the mapped host buffer map
+// when they number at most map_cap, else to the device buffer stage.
+constexpr long long kMappedRecords = 1LL << 18;  // mapped host records per net
 cudaError_t launch_drain_records(const StepParams& p, int nreg, unsigned long long* pre,
                                  unsigned long long* stage, unsigned long long* header,
-                                 cudaStream_t st);
+                                 unsigned long long* map_hdr, unsigned long long* map,
+                                 long long map_cap, cudaStream_t st);
 size_t batch_smem(int max_npc);
 int batch_grid(int precision, int infl, int num_sms, int max_npc);
 cudaError_t launch_batch(const BatchParams& b, int precision, int infl, int grid, int max_npc,

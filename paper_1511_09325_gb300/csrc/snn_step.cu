@@ -758,11 +758,13 @@ __global__ void __launch_bounds__(kDeliverThreads, 3) batch_kernel(const BatchPa
 
 // Spike-record drain, first kernel (one block): pre[b] = records kept in the
 // regions before b; header[0] = records kept, header[1] = 1 if any were
-// dropped; clears the overflow flag.
+// dropped (also written to the mapped host header map_hdr); clears the
+// overflow flag.
 __global__ void __launch_bounds__(1024) scan_records_kernel(const unsigned long long* rcnt,
                                                             int nreg, long long region, Ctl* ctl,
                                                             unsigned long long* pre,
-                                                            unsigned long long* header) {
+                                                            unsigned long long* header,
+                                                            unsigned long long* map_hdr) {
   __shared__ unsigned long long s_w[32];
   __shared__ unsigned s_l[32];
   const int per = (nreg + blockDim.x - 1) / blockDim.x;
@@ -801,22 +803,27 @@ __global__ void __launch_bounds__(1024) scan_records_kernel(const unsigned long 
     run += (long long)v < region ? v : (unsigned long long)region;
   }
   if (threadIdx.x == blockDim.x - 1) {
+    const unsigned long long lost = (any || ctl->rec_overflow) ? 1ull : 0ull;
     header[0] = before + incl;
-    header[1] = (any || ctl->rec_overflow) ? 1ull : 0ull;
+    header[1] = lost;
+    map_hdr[0] = before + incl;
+    map_hdr[1] = lost;
     ctl->rec_overflow = 0u;
   }
 }
 
 // Spike-record drain, second kernel: block b copies the records kept in
-// region b to stage[pre[b] ...] and empties the region.
+// region b to position pre[b] of the mapped host buffer map (when all kept
+// records fit in it) or of stage, and empties the region.
 __global__ void copy_records_kernel(unsigned long long* rcnt, long long region,
                                     const unsigned long long* rec, const unsigned long long* pre,
-                                    unsigned long long* stage) {
+                                    const unsigned long long* header, unsigned long long* stage,
+                                    unsigned long long* map, long long map_cap) {
   const int b = blockIdx.x;
   const unsigned long long v = rcnt[b];
   const long long kept = (long long)v < region ? (long long)v : region;
   const unsigned long long* src = rec + (long long)b * region;
-  unsigned long long* dst = stage + pre[b];
+  unsigned long long* dst = ((long long)header[0] <= map_cap ? map : stage) + pre[b];
   for (long long k = threadIdx.x; k < kept; k += blockDim.x) dst[k] = src[k];
   __syncthreads();
   if (threadIdx.x == 0) rcnt[b] = 0ull;
@@ -881,11 +888,14 @@ cudaError_t launch_deliver(const StepParams& p, int precision, int grid, cudaStr
 
 cudaError_t launch_drain_records(const StepParams& p, int nreg, unsigned long long* pre,
                                  unsigned long long* stage, unsigned long long* header,
-                                 cudaStream_t st) {
-  scan_records_kernel<<<1, 1024, 0, st>>>(p.rcnt, nreg, p.rec_region, p.ctl, pre, header);
+                                 unsigned long long* map_hdr, unsigned long long* map,
+                                 long long map_cap, cudaStream_t st) {
+  scan_records_kernel<<<1, 1024, 0, st>>>(p.rcnt, nreg, p.rec_region, p.ctl, pre, header,
+                                          map_hdr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  copy_records_kernel<<<nreg, 256, 0, st>>>(p.rcnt, p.rec_region, p.rec, pre, stage);
+  copy_records_kernel<<<nreg, 256, 0, st>>>(p.rcnt, p.rec_region, p.rec, pre, header, stage, map,
+                                            map_cap);
   return cudaGetLastError();
 }
 
