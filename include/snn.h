@@ -253,7 +253,7 @@ snn_net* snn_batch_net(snn_batch* batch, int k);
 
 /*
  * snn_batch_tune -- pick the fastest delivery schedule for this batch (16-byte
- * chunks in flight per lane: 4 or 2; per-warp shared windows: on or off) by
+ * chunks in flight per lane: 4 or 2; shared-memory windows: on or off) by
  * timing two interleaved rounds of steps_per_trial steps of each.  The trial
  * steps advance the simulation (all schedules compute identical sums).
  * *choice (may be NULL) receives the pick, 0..3.

@@ -36,6 +36,7 @@ namespace {
 
 constexpr int kUpdateThreads = 256;
 constexpr int kDeliverThreads = 256;
+constexpr int kBatchThreads = kUpdateThreads;  // the batch kernel runs both bodies
 constexpr int kInflight = 4;  // 16-byte synapse chunks in flight per lane
 constexpr int kTile = kUpdateThreads * 4;    // neurons per update tile
 constexpr int kTileCols = kTile / 2 + 2;     // columns a tile can touch (npc >= 2)
@@ -295,8 +296,9 @@ __device__ __forceinline__ int wrap_near(int v, int n) {
 }
 
 constexpr int kWindows = 4;        // shared-memory windows (columns) per delivery block
-constexpr int kTabEntries = 1024;  // (column, bucket) entries per table piece
-constexpr int kDeliverWarps = kDeliverThreads / 32;
+constexpr int kBatchItems = 16;    // items per warp batch (at most 32)
+// (column, bucket) entries per table piece, at most: 4 per thread
+constexpr int kTabEntries = 4 * (kDeliverThreads > kBatchThreads ? kDeliverThreads : kBatchThreads);
 
 // Per-item info travelling with a chunk: the spiker's column cx | cy << 14
 // and whether it is inhibitory (bit 28).
@@ -337,7 +339,7 @@ __device__ __forceinline__ void deliver_record(uint32_t code, uint32_t wbits, ui
 struct DeliverSmem {
   unsigned tab[kTabEntries + 1];  // items before each (column, bucket) entry of the piece
   int slot[kMaxDelays];           // slot of each bucket's step, -1 before step 0
-  unsigned long long wsum[kDeliverWarps];
+  unsigned long long wsum[32];    // per-warp sums of block_scan
   unsigned long long xgp[2];      // items before the group holding lo / hi - 1
   unsigned long long p0;          // items before column c0
   int xg[2];                      // group holding lo / hi - 1
@@ -351,6 +353,7 @@ constexpr size_t kDeliverSmemPad = (sizeof(DeliverSmem) + 255) / 256 * 256;
 __device__ __forceinline__ unsigned long long block_scan(unsigned long long v, DeliverSmem& S,
                                                          unsigned long long* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (int)(blockDim.x >> 5);
   unsigned long long incl = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -360,8 +363,7 @@ __device__ __forceinline__ unsigned long long block_scan(unsigned long long v, D
   if (lane == 31) S.wsum[warp] = incl;
   __syncthreads();
   unsigned long long before = 0ull, all = 0ull;
-#pragma unroll
-  for (int w = 0; w < kDeliverWarps; ++w) {
+  for (int w = 0; w < nwarps; ++w) {
     const unsigned long long s = S.wsum[w];
     before += w < warp ? s : 0ull;
     all += s;
@@ -491,10 +493,10 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
 // ranges; block vb locates the first and last column of its range from the
 // group and column counts (gsum, isum), tabulates the (column, bucket) counts
 // of those columns (in pieces of at most kTabEntries entries) and lets its
-// warps take batches of 32 items.  With P.agg the synapses onto the first
-// kWindows columns of each piece, from any of the piece's items, are summed
-// in shared memory (win_base, kWindows * n_per_col ints) and flushed once per
-// piece.
+// warps take batches of kBatchItems items.  With P.agg the synapses onto the
+// first kWindows columns of each piece, from any of the piece's items, are
+// summed in shared memory (win_base, kWindows * n_per_col ints) and flushed
+// once per piece.
 template <int PREC, int INFL>
 __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, int vb, int vgrid,
                                              DeliverSmem& S, int32_t* win_base) {
@@ -574,7 +576,8 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
 
   const uint64_t pol = evict_last_policy();
   const uint32_t win_s = (uint32_t)__cvta_generic_to_shared(win_base);
-  const int cols_per_piece = kTabEntries / P.ndel;
+  // a piece tabulates at most 4 entries per thread
+  const int cols_per_piece = min(kTabEntries, 4 * (int)blockDim.x) / P.ndel;
   unsigned long long pbase = S.p0;  // items before the piece's first column
   for (int pc = c0; pc <= c1; pc += cols_per_piece) {
     const int ncp = min(cols_per_piece, c1 - pc + 1);
@@ -611,10 +614,12 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
     const uint32_t wlen = P.agg ? (uint32_t)min(kWindows, ncp) * (uint32_t)P.npc : 0u;
     while (a < b) {
       unsigned k0 = 0u;
-      if (lane == 0) k0 = atomicAdd(&S.next, 32u);
+      if (lane == 0) k0 = atomicAdd(&S.next, (unsigned)kBatchItems);
       k0 = __shfl_sync(0xFFFFFFFFu, k0, 0);
       if (a + k0 >= b) break;
-      deliver_batch<PREC, INFL>(P, a + k0 + lane, b, S, n_entries, pc, win_s, wbase, wlen, pol);
+      const unsigned end = min(b, a + k0 + (unsigned)kBatchItems);
+      deliver_batch<PREC, INFL>(P, lane < kBatchItems ? a + k0 + lane : end, end, S, n_entries, pc,
+                                win_s, wbase, wlen, pol);
     }
     __syncthreads();
     // flush the windows with coalesced reductions, leaving them zeroed
@@ -716,7 +721,7 @@ __device__ __forceinline__ int net_of(const int* first, int n, int g) {
 }
 
 template <int PREC, int INFL>
-__global__ void __launch_bounds__(kDeliverThreads, 3) batch_kernel(const BatchParams B) {
+__global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchParams B) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ StepParams s_p;  // the current virtual block's net
   __shared__ int s_uf[kMaxBatch + 1], s_df[kMaxBatch + 1];
@@ -921,7 +926,7 @@ int batch_grid(int precision, int infl, int num_sms, int max_npc) {
   void* fn = batch_kernel_ptr(precision, infl);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kDeliverThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, smem);
   return per_sm * num_sms;
 }
 
@@ -929,7 +934,7 @@ cudaError_t launch_batch(const BatchParams& b, int precision, int infl, int grid
                          cudaStream_t st) {
   void* args[] = {const_cast<BatchParams*>(&b)};
   return cudaLaunchCooperativeKernel(batch_kernel_ptr(precision, infl), dim3(grid),
-                                     dim3(kDeliverThreads), args, batch_smem(max_npc), st);
+                                     dim3(kBatchThreads), args, batch_smem(max_npc), st);
 }
 
 cudaError_t launch_sum_parts(const unsigned long long* part, int n, unsigned long long* out,
