@@ -302,10 +302,11 @@ def run_ours(args):
     P = K if args.profile_steps is None else min(args.profile_steps, K)
     roofline = _kernel_roofline(snn, torch, cfg, seed, stream, Wm, max(1, P), args.workload)
 
-    extra = batched = None
+    extra = batched = surrogate = None
     if not args.no_extra and ws == 1:
         extra = _precision_form(snn, torch, stream, Wm)
         batched = _batched_form(snn, torch, stream)
+        surrogate = _surrogate_form(snn, torch, stream)
     cpu = None
     if ws == 1 and not args.no_cpu:
         cb = _cpu_baseline(args.workload)
@@ -340,9 +341,38 @@ def run_ours(args):
             line["precision_form"] = extra
         if batched:
             line["batched_form"] = batched
+        if surrogate:
+            line["surrogate_gradient"] = surrogate
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _surrogate_form(snn, torch, stream, steps=500, ckpt=50):
+    """The differentiable form on 4x4 columns (19 840 neurons, 24.6 M
+    synapses, seed 11): 500 steps, checkpoints every 50, hard spikes with the
+    surrogate derivative; time of the forward pass alone and of forward plus
+    checkpointed backward (the library call synchronises)."""
+    theta = [1.0, 1.0, 1.0, 1.0, 0.02, 2.5]
+    n, s = W.neuron_params(), W.synapse_params()
+    out = {"workload": "cols4x4", "steps": steps, "checkpoint_every": ckpt, "mode": "hard"}
+    net = snn.Net(4, 4, n, s, 11, "f32w", stream=stream.cuda_stream)
+    g = snn.Grad(net, steps, checkpoint_every=ckpt, hard=True)
+    g.loss_and_grad(theta)  # warm-up
+    t0 = time.perf_counter()
+    for _ in range(3):
+        loss, rates = g.loss(theta)
+    fwd = (time.perf_counter() - t0) / 3
+    t0 = time.perf_counter()
+    for _ in range(3):
+        loss, rates, grad = g.loss_and_grad(theta)
+    both = (time.perf_counter() - t0) / 3
+    g.close()
+    net.close()
+    out.update(forward_ms=fwd * 1e3, forward_backward_ms=both * 1e3,
+               forward_backward_ms_per_step=both * 1e3 / steps, loss=loss,
+               rates_hz=[float(x) for x in rates], grad=[float(x) for x in grad])
+    return out
 
 
 def _batched_form(snn, torch, stream, steps=2000, n_nets=64):

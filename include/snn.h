@@ -272,6 +272,56 @@ const char* snn_batch_last_error(const snn_batch* batch);
 /* snn_batch_destroy -- free the batch and its members; NULL is a no-op. */
 void snn_batch_destroy(snn_batch* batch);
 
+/*
+ * Differentiable form (surrogate gradient).  The paper simulates the spiking
+ * network only (Sec. 2); this is the standard surrogate-gradient extension of
+ * the same recursion, on the net's own synapse table, with respect to six
+ * parameters theta = {a_EE, a_EI, a_IE, a_II, g_c, nu_ext}: a_XY multiplies
+ * every synaptic weight from population X onto population Y (1 = the net as
+ * built), g_c replaces the excitatory adaptation strength (mV/ms) and nu_ext
+ * (kHz) the external rate.  The external input becomes its Gaussian form
+ * J (lam + sqrt(lam) xi), lam = nu_ext * 1 ms, xi a normal draw of Philox
+ * stream 4 (key = the net's seed, counter (i/4, t, 4, 0), word i mod 4, mapped
+ * through the 65536-entry normal quantile table), so that nu_ext has a
+ * pathwise derivative.  Per step, neuron i of population p:
+ *   I = a[E][p] X_E + a[I][p] X_I + J (lam + sqrt(lam) xi)     (X_P: input
+ *       from sources of population P, each synapse weighted by s_j(t - d))
+ *   g = max(0, 1 - s(t-1) - s(t-2)),  U = g (V + I) + (1 - g) V_reset
+ *   s = [U >= theta] (hard = 1) or sigmoid(beta (U - theta)) (hard = 0)
+ *   V' = U - s (U - V_reset),  c' = c + dc s,
+ *   V <- P_VV V' + P_VC c',  c <- P_CC c'
+ * from the net's initial potentials (c = 0), for n_steps steps.  The loss is
+ * (r_E - r_E*)^2 + (r_I - r_I*)^2 with r_P = 1000 * mean of s over
+ * population P and all steps (Hz).  Hard mode differentiates with the
+ * surrogate ds/dU = 1 / (1 + beta |U - theta|)^2 (the spikes are exactly those
+ * of the threshold rule); soft mode with the exact derivative.
+ *
+ * snn_grad_build -- a differentiable view of `net` (which must be
+ * SNN_EXACT_F32W and outlive the view).  checkpoint_every: steps between
+ * stored states; the backward pass recomputes each segment from its
+ * checkpoint (device memory ~ N * (8 * checkpoint_every + 23 * n_steps /
+ * checkpoint_every) floats).  target_rates (Hz, E then I) may be NULL for
+ * (3, 8).  Runs on the net's stream.
+ */
+typedef struct snn_grad snn_grad; /* opaque, library-owned */
+int snn_grad_build(snn_net* net, int64_t n_steps, int32_t checkpoint_every, int32_t hard,
+                   float beta, const double* target_rates, snn_grad** out);
+
+/*
+ * snn_grad_run -- forward pass for theta[6] (host doubles): *loss and, when
+ * not NULL, rates[2] (Hz).  When grad is not NULL also the backward pass:
+ * grad[6] = d loss / d theta.  Deterministic: every reduction has a fixed
+ * order.  Synchronises the net's stream.  SNN_EINVAL for a NULL loss or
+ * theta, non-finite parameters or nu_ext <= 0.
+ */
+int snn_grad_run(snn_grad* g, const double* theta, double* loss, double* rates, double* grad);
+
+/* snn_grad_last_error -- message of the last failure on g ("" if none). */
+const char* snn_grad_last_error(const snn_grad* g);
+
+/* snn_grad_destroy -- free the view (not the net); NULL is a no-op. */
+void snn_grad_destroy(snn_grad* g);
+
 /* snn_last_error -- message of the last failure on net (thread-local when net
  * is NULL).  Never NULL; valid until the next call on the same net. */
 const char* snn_last_error(const snn_net* net);

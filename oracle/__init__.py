@@ -77,10 +77,12 @@ def lib():
                                        ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int64, vp, vp, vp, vp, vp]
         L.orc_init_v.argtypes = [P(OrcParams), ctypes.c_int, ctypes.c_int64, ctypes.c_int64, vp]
+        L.orc_surr_xi.argtypes = [P(OrcParams), ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_int64, vp]
         L.orc_run.argtypes = [P(OrcParams), ctypes.c_int, ctypes.c_int64,
                               ctypes.c_int64] + [vp] * 8
         for f in ("orc_validate", "orc_tables_export", "orc_synapses", "orc_init_v",
-                  "orc_ext_counts", "orc_neuron_trace", "orc_run"):
+                  "orc_ext_counts", "orc_neuron_trace", "orc_run", "orc_surr_xi"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -167,6 +169,13 @@ def ext_counts(p, i0, n, t0, n_steps=None):
     k = np.zeros(nt * n, np.int32)
     _check(lib().orc_ext_counts(ctypes.byref(p), i0, n, t0, nt, _ptr(k)), "ext_counts")
     return k if n_steps is None else k.reshape(nt, n)
+
+
+def surr_xi(p, i0, n, t0, n_steps):
+    """Normal draws xi[t][i] of the relaxed network (Philox stream SURR)."""
+    xi = np.zeros(n_steps * n, np.float64)
+    _check(lib().orc_surr_xi(ctypes.byref(p), i0, n, t0, n_steps, _ptr(xi)), "surr_xi")
+    return xi.reshape(n_steps, n)
 
 
 def init_v(p, mode, i0, n):

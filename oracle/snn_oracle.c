@@ -44,6 +44,7 @@
 #define TAG_CONN 1u
 #define TAG_EXT 2u
 #define TAG_INIT 3u
+#define TAG_SURR 4u /* normal draws of the relaxed (differentiable) network */
 
 #define POIS_CAP 128 /* table entries; lambda is limited so that it saturates */
 #define Q_SIZE 65536
@@ -471,6 +472,28 @@ int orc_ext_counts(const orc_params *p, int64_t i0, int64_t n, int64_t t0,
   for (t = 0; t < nt; ++t)
     for (i = 0; i < n; ++i)
       k[t * n + i] = poisson_k(&tb, ext_word(p->seed, i0 + i, t0 + t));
+  free_tables(&tb);
+  return ORC_OK;
+}
+
+/* Standard-normal draws of the relaxed network (reading: the external
+ * Poisson input is replaced by its Gaussian approximation, whose normal
+ * variate is the quantile-table value of the top 16 bits of word i mod 4 of
+ * Philox(seed; i/4, t, SURR)).  xi[t][i] for t0 <= t < t0 + nt. */
+int orc_surr_xi(const orc_params *p, int64_t i0, int64_t n, int64_t t0, int64_t nt,
+                double *xi) {
+  orc_tables tb;
+  int64_t i, t;
+  uint32_t x[4];
+  int rc = validate(p);
+  if (rc) return rc;
+  rc = make_tables(p, &tb);
+  if (rc) return rc;
+  for (t = 0; t < nt; ++t)
+    for (i = 0; i < n; ++i) {
+      draw(p->seed, (uint32_t)((i0 + i) >> 2), (uint32_t)(t0 + t), TAG_SURR, x);
+      xi[t * n + i] = tb.q[x[(i0 + i) & 3] >> 16];
+    }
   free_tables(&tb);
   return ORC_OK;
 }

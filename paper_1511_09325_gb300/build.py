@@ -23,7 +23,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler",
 GXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", INCLUDE,
              "-I", CSRC]
 
-CU_SOURCES = ["snn_build.cu", "snn_step.cu", "snn_api.cu", "snn_noalloc.cu"]
+CU_SOURCES = ["snn_build.cu", "snn_step.cu", "snn_api.cu", "snn_noalloc.cu", "snn_grad.cu"]
 CXX_SOURCES = ["snn_tables.cpp"]
 
 

@@ -21,6 +21,7 @@ struct snn_net {
   int deliver_grid = 0;
   long long N = 0, Npad = 0, ncol = 0;
   uint64_t seed = 0;
+  snn_neuron_params neuron{};
   HostTables tables;
   StepParams sp{};
   // device memory
@@ -258,6 +259,7 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   net->nslot = sp->d_max + 1;
   net->precision = precision;
   net->seed = seed;
+  net->neuron = *np;
   net->ncol = (long long)gw * gh;
   net->N = net->ncol * np->n_per_col;
   net->Npad = (net->N + 3) / 4 * 4;
@@ -365,6 +367,28 @@ Ctl read_ctl(snn_net* net, cudaError_t* e) {
 }
 
 }  // namespace
+
+namespace snn {
+
+int net_view(snn_net* net, NetView* v) {
+  if (!net) return SNN_EINVAL;
+  v->syn = net->syn;
+  v->bend = net->bend;
+  v->N = net->N;
+  v->npc = net->npc;
+  v->nexc = net->nexc;
+  v->dmin = net->dmin;
+  v->ndel = net->ndel;
+  v->rowcap = net->rowcap;
+  v->precision = net->precision;
+  v->num_sms = net->num_sms;
+  v->seed = net->seed;
+  v->neuron = net->neuron;
+  v->stream = net->stream;
+  return SNN_OK;
+}
+
+}  // namespace snn
 
 extern "C" {
 

@@ -46,6 +46,7 @@ namespace snn {
 constexpr uint32_t kTagConn = 1u;  // Philox counter word 2 of each stream
 constexpr uint32_t kTagExt = 2u;
 constexpr uint32_t kTagInit = 3u;
+constexpr uint32_t kTagSurr = 4u;  // normal draws of the differentiable form
 constexpr int kMaxDelays = 32;   // d_max <= 32
 constexpr int kBendStride = 32;  // bytes of bucket ends per neuron
 constexpr int kSlotUnit = 8;     // buckets are padded to 8 synapse slots
@@ -74,6 +75,8 @@ int make_host_tables(const snn_neuron_params& np, const snn_synapse_params& sp,
                      int precision, HostTables* out, std::string* err);
 // The neuron-update part only: Poisson table, propagators, J_ext, refractory.
 int make_neuron_tables(const snn_neuron_params& np, HostTables* out, std::string* err);
+// Standard-normal quantiles at (m + 0.5) / 65536, m < 65536 (computed once).
+const std::vector<double>& quantile_table();
 
 // Device control block.
 struct Ctl {
@@ -140,6 +143,18 @@ struct BuildParams {
   void* syn;
   uint8_t* bend;
 };
+
+// What the differentiable form reads of a net (snn_api.cu fills it).
+struct NetView {
+  const void* syn;
+  const uint8_t* bend;
+  long long N;
+  int npc, nexc, dmin, ndel, rowcap, precision, num_sms;
+  uint64_t seed;
+  snn_neuron_params neuron;
+  cudaStream_t stream;
+};
+int net_view(snn_net* net, NetView* v);
 
 // Shared host helpers (snn_api.cu).
 int fail_global(int code, const std::string& msg);

@@ -185,4 +185,6 @@ int make_host_tables(const snn_neuron_params& np, const snn_synapse_params& sp,
   return SNN_OK;
 }
 
+const std::vector<double>& quantile_table() { return normal_quantiles(); }
+
 }  // namespace snn

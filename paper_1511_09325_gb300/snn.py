@@ -24,6 +24,7 @@ EXPORTS = ("snn_build", "snn_step", "snn_read_spikes", "snn_pending_spikes",
            "snn_read_synapses", "snn_info", "snn_step_profiled", "snn_update_noalloc",
            "snn_batch_build", "snn_batch_step", "snn_batch_net", "snn_batch_tune",
            "snn_batch_set_wait", "snn_batch_last_error", "snn_batch_destroy",
+           "snn_grad_build", "snn_grad_run", "snn_grad_last_error", "snn_grad_destroy",
            "snn_last_error", "snn_destroy")
 
 
@@ -87,13 +88,20 @@ def load(path=LIB_PATH):
     L.snn_batch_last_error.restype = ctypes.c_char_p
     L.snn_batch_destroy.argtypes = [vp]
     L.snn_batch_destroy.restype = None
+    L.snn_grad_build.argtypes = [vp, i64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, vp,
+                                 P(vp)]
+    L.snn_grad_run.argtypes = [vp, vp, P(ctypes.c_double), vp, vp]
+    L.snn_grad_last_error.argtypes = [vp]
+    L.snn_grad_last_error.restype = ctypes.c_char_p
+    L.snn_grad_destroy.argtypes = [vp]
+    L.snn_grad_destroy.restype = None
     L.snn_last_error.argtypes = [vp]
     L.snn_last_error.restype = ctypes.c_char_p
     L.snn_destroy.argtypes = [vp]
     L.snn_destroy.restype = None
     for f in EXPORTS:
         if f not in ("snn_last_error", "snn_destroy", "snn_batch_net", "snn_batch_last_error",
-                     "snn_batch_destroy"):
+                     "snn_batch_destroy", "snn_grad_last_error", "snn_grad_destroy"):
             getattr(L, f).restype = i32
     _lib = L
     return L
@@ -237,6 +245,89 @@ def _bcheck(rc, handle, ok=(SNN_OK,)):
     if rc not in ok:
         raise SnnError(rc, load().snn_batch_last_error(handle).decode())
     return rc
+
+
+GRAD_PARAMS = ("a_EE", "a_EI", "a_IE", "a_II", "g_c", "nu_ext")
+
+
+def snn_grad_build(handle, n_steps, checkpoint_every=50, hard=True, beta=5.0,
+                   target_rates=(3.0, 8.0)):
+    """Differentiable view of an F32W net; returns the opaque handle."""
+    h = ctypes.c_void_p()
+    tr = np.array(target_rates, np.float64)
+    _check(load().snn_grad_build(handle, int(n_steps), int(checkpoint_every), 1 if hard else 0,
+                                 float(beta), _p(tr), ctypes.byref(h)), None)
+    return h.value
+
+
+def snn_grad_run(handle, theta, want_grad=True):
+    """(loss, rates[2], grad[6] or None) for theta[6]."""
+    th = np.ascontiguousarray(theta, np.float64)
+    loss = ctypes.c_double()
+    rates = np.zeros(2, np.float64)
+    grad = np.zeros(6, np.float64) if want_grad else None
+    rc = load().snn_grad_run(handle, _p(th), ctypes.byref(loss), _p(rates), _p(grad))
+    if rc != SNN_OK:
+        raise SnnError(rc, load().snn_grad_last_error(handle).decode())
+    return loss.value, rates, grad
+
+
+def snn_grad_destroy(handle):
+    if handle:
+        load().snn_grad_destroy(handle)
+
+
+class Grad:
+    """Loss and gradient of the net's differentiable form (see include/snn.h)."""
+
+    def __init__(self, net, n_steps, checkpoint_every=50, hard=True, beta=5.0,
+                 target_rates=(3.0, 8.0)):
+        self.net = net  # the view reads the net's synapse table: keep it alive
+        self.handle = snn_grad_build(net.handle, n_steps, checkpoint_every, hard, beta,
+                                     target_rates)
+
+    def loss(self, theta):
+        return snn_grad_run(self.handle, theta, want_grad=False)[:2]
+
+    def loss_and_grad(self, theta):
+        return snn_grad_run(self.handle, theta, want_grad=True)
+
+    def close(self):
+        if self.handle:
+            snn_grad_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rate_loss(grad_view, theta):
+    """The differentiable form as a torch function of a 6-element parameter
+    tensor: forward and backward both run in the CUDA library."""
+    import torch
+
+    class _RateLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, th):
+            loss, _, g = grad_view.loss_and_grad(th.detach().double().cpu().numpy())
+            ctx.save_for_backward(torch.as_tensor(g, dtype=th.dtype, device=th.device))
+            return torch.as_tensor(loss, dtype=th.dtype, device=th.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            return gout * g
+
+    return _RateLoss.apply(theta)
 
 
 class Member:
