@@ -21,7 +21,8 @@
 //
 // Forward: grad_deliver_kernel (one warp per source row, pull by delay: the
 // input of step t is every bucket d of every row weighted by s_j(t - d), summed
-// as int64 fixed point in 2^-32 mV, so the sums do not depend on the order)
+// as int64 fixed point in 2^-32 mV, so the sums do not depend on the order;
+// rows whose last d_max spikes are all zero leave after one load)
 // and grad_update_kernel (one thread per neuron; hard mode is the spiking
 // model's arithmetic, one float rounding per operation).  The state (V, c and
 // the spike history of d_max + 1 steps) is checkpointed every `ckpt` steps.
@@ -99,32 +100,63 @@ __global__ void __launch_bounds__(kThreads) grad_init_kernel(const GradParams P)
   P.C[i] = 0.f;
 }
 
+// Bucket ends (slots) in lanes 0..ndel-1 of the warp; the bucket holding
+// slot k is the first b with end_b > k, found by a fixed five-step search
+// over the lanes (every lane takes part, whatever its k).
+__device__ __forceinline__ int bucket_of(int k, int end_lane, int ndel) {
+  int lo = 0, hi = ndel - 1;
+#pragma unroll
+  for (int step = 0; step < 5; ++step) {
+    const int mid = (lo + hi) >> 1;
+    const int e = __shfl_sync(0xFFFFFFFFu, end_lane, mid);
+    if (e > k)
+      hi = mid;
+    else
+      lo = min(mid + 1, hi);
+  }
+  return lo;
+}
+
 // Input of step t: every bucket d of every source row j, weighted by
-// s_j(t - d), into the row's population accumulator.  One warp per row.
+// s_j(t - d), into the row's population accumulator.  One warp per row: the
+// lanes first load the row's ndel spike values at once and the warp leaves
+// when all are zero; otherwise it streams the row four records per lane
+// (16-byte loads; a bucket is a whole number of 8-slot units, so the four
+// records of a lane share a bucket).
 __global__ void __launch_bounds__(kThreads) grad_deliver_kernel(const GradParams P, long long t) {
   const long long j = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (j >= P.N) return;
+  float s_lane = 0.f;
+  int end_lane = 0x7FFFFFFF;
+  if (lane < P.ndel) {
+    const long long src = t - (P.dmin + lane);
+    s_lane = src >= 0 ? P.shist[(src % P.nslot) * P.N + j] : 0.f;
+    end_lane = (int)P.bend[j * kBendStride + lane] * kSlotUnit;
+  }
+  if (__ballot_sync(0xFFFFFFFFu, s_lane != 0.f) == 0u) return;
   const bool exc = (int)(j % P.npc) < P.nexc;
   unsigned long long* acc = exc ? P.xe : P.xin;
-  const uint8_t* be = P.bend + j * kBendStride;
+  const int row_end = __shfl_sync(0xFFFFFFFFu, end_lane, P.ndel - 1);
   const uint2* row = P.syn + j * (long long)P.rowcap;
-  int beg = 0;
-  for (int b = 0; b < P.ndel; ++b) {
-    const int end = (int)be[b] * kSlotUnit;
-    const long long src = t - (P.dmin + b);
-    const float s = src >= 0 ? P.shist[(src % P.nslot) * P.N + j] : 0.f;
-    if (s != 0.f) {
-      for (int k = beg + lane; k < end; k += 32) {
-        const uint2 r = row[k];
-        if (r.x == kPad) continue;
-        const int32_t wfx = (int32_t)r.y;
+  for (int k0 = 0; k0 < row_end; k0 += 128) {
+    const int k = k0 + 4 * lane;
+    const int b = bucket_of(k, end_lane, P.ndel);
+    const float s = __shfl_sync(0xFFFFFFFFu, s_lane, b);
+    if (k < row_end && s != 0.f) {
+      const uint4 r01 = __ldcs(reinterpret_cast<const uint4*>(row + k));
+      const uint4 r23 = __ldcs(reinterpret_cast<const uint4*>(row + k + 2));
+      const uint32_t tg[4] = {r01.x, r01.z, r23.x, r23.z};
+      const uint32_t wf[4] = {r01.y, r01.w, r23.y, r23.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (tg[q] == kPad) continue;
+        const int32_t wfx = (int32_t)wf[q];
         const long long v = P.hard ? (long long)wfx * 65536ll
                                    : __float2ll_rn(__fmul_rn(__fmul_rn(s, (float)wfx), 65536.f));
-        atomicAdd(acc + r.x, (unsigned long long)v);
+        atomicAdd(acc + tg[q], (unsigned long long)v);
       }
     }
-    beg = end;
   }
 }
 
@@ -203,30 +235,40 @@ __global__ void __launch_bounds__(kThreads) grad_update_kernel(const GradParams 
 }
 
 // Adjoint of s_j(tau) through its outgoing synapses: sum over buckets d with
-// tau + d < T of w * (a[p_j][p_i] * adjoint of I_i(tau + d)).  One warp per row,
-// fixed summation order.
+// tau + d < T of w * (a[p_j][p_i] * adjoint of I_i(tau + d)).  One warp per
+// row, four records per lane per pass (16-byte loads), a fixed summation
+// order.
 __global__ void __launch_bounds__(kThreads) grad_gather_kernel(const GradParams P, long long tau) {
   const long long j = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (j >= P.N) return;
   const bool exc = (int)(j % P.npc) < P.nexc;
   const float* ib = exc ? P.ibe : P.ibi;
-  const uint8_t* be = P.bend + j * kBendStride;
+  long long off_lane = -1;  // ring offset of bucket `lane`'s step, -1 beyond T
+  int end_lane = 0x7FFFFFFF;
+  if (lane < P.ndel) {
+    const long long dst = tau + P.dmin + lane;
+    off_lane = dst < P.T ? (dst % P.nslot) * P.N : -1;
+    end_lane = (int)P.bend[j * kBendStride + lane] * kSlotUnit;
+  }
+  const int row_end = __shfl_sync(0xFFFFFFFFu, end_lane, P.ndel - 1);
   const uint2* row = P.syn + j * (long long)P.rowcap;
   float acc = 0.f;
-  int beg = 0;
-  for (int b = 0; b < P.ndel; ++b) {
-    const int end = (int)be[b] * kSlotUnit;
-    const long long dst = tau + P.dmin + b;
-    if (dst < P.T) {
-      const float* ibs = ib + (dst % P.nslot) * P.N;
-      for (int k = beg + lane; k < end; k += 32) {
-        const uint2 r = row[k];
-        if (r.x == kPad) continue;
-        acc = __fmaf_rn((float)(int32_t)r.y, ibs[r.x], acc);
-      }
+#pragma unroll 2
+  for (int k0 = 0; k0 < row_end; k0 += 128) {
+    const int k = k0 + 4 * lane;
+    const int b = bucket_of(k, end_lane, P.ndel);
+    const long long off = __shfl_sync(0xFFFFFFFFu, off_lane, b);
+    if (k < row_end && off >= 0) {
+      const uint4 r01 = __ldcs(reinterpret_cast<const uint4*>(row + k));
+      const uint4 r23 = __ldcs(reinterpret_cast<const uint4*>(row + k + 2));
+      const float* ibs = ib + off;
+      const uint32_t tg[4] = {r01.x, r01.z, r23.x, r23.z};
+      const uint32_t wf[4] = {r01.y, r01.w, r23.y, r23.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (tg[q] != kPad) acc = __fmaf_rn((float)(int32_t)wf[q], ibs[tg[q]], acc);
     }
-    beg = end;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
