@@ -38,7 +38,9 @@ class OrcParams(ctypes.Structure):
         ("w_exc", ctypes.c_float), ("w_inh", ctypes.c_float),
         ("w_cv", ctypes.c_float), ("d_min", ctypes.c_int32),
         ("d_max", ctypes.c_int32), ("h", ctypes.c_double),
-        ("seed", ctypes.c_uint64),
+        ("seed", ctypes.c_uint64), ("connectivity", ctypes.c_int32),
+        ("p_local", ctypes.c_float), ("remote_a", ctypes.c_float),
+        ("remote_sigma", ctypes.c_float), ("remote_cutoff", ctypes.c_float),
     ]
 
 
@@ -79,10 +81,14 @@ def lib():
         L.orc_init_v.argtypes = [P(OrcParams), ctypes.c_int, ctypes.c_int64, ctypes.c_int64, vp]
         L.orc_surr_xi.argtypes = [P(OrcParams), ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.c_int64, vp]
+        L.orc_paper_tables.argtypes = [P(OrcParams)] + [vp] * 6
+        L.orc_paper_synapses.argtypes = [P(OrcParams), ctypes.c_int, ctypes.c_int64,
+                                         ctypes.c_int64, ctypes.c_int64] + [vp] * 7
         L.orc_run.argtypes = [P(OrcParams), ctypes.c_int, ctypes.c_int64,
                               ctypes.c_int64] + [vp] * 8
         for f in ("orc_validate", "orc_tables_export", "orc_synapses", "orc_init_v",
-                  "orc_ext_counts", "orc_neuron_trace", "orc_run", "orc_surr_xi"):
+                  "orc_ext_counts", "orc_neuron_trace", "orc_run", "orc_surr_xi",
+                  "orc_paper_tables", "orc_paper_synapses"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -107,6 +113,11 @@ def make_params(grid_w, grid_h, neuron, synapse, seed, h=1.0):
     p.d_min, p.d_max = synapse["d_min"], synapse["d_max"]
     p.h = h
     p.seed = seed
+    p.connectivity = synapse.get("connectivity", 0)
+    p.p_local = synapse.get("p_local", 0.8)
+    p.remote_a = synapse.get("remote_a", 0.05)
+    p.remote_sigma = synapse.get("remote_sigma", 1.0)
+    p.remote_cutoff = synapse.get("remote_cutoff", 0.001)
     return p
 
 
@@ -161,6 +172,42 @@ def synapses(p, mode, j0, n):
     sh = (n, K)
     return dict(target=tgt.reshape(sh), delay=dly.reshape(sh), wfx=wfx.reshape(sh),
                 w=w.reshape(sh), dx=dx.reshape(sh), dy=dy.reshape(sh))
+
+
+def paper_tables(p):
+    """The paper law's kept remote offsets, their thresholds, the local
+    threshold and the number of candidates per neuron."""
+    n_off = ctypes.c_int32()
+    dx = np.zeros(64, np.int32)
+    dy = np.zeros(64, np.int32)
+    thr = np.zeros(64, np.uint64)
+    lthr = ctypes.c_uint64()
+    nc = ctypes.c_int64()
+    _check(lib().orc_paper_tables(ctypes.byref(p), ctypes.byref(n_off), _ptr(dx), _ptr(dy),
+                                  _ptr(thr), ctypes.byref(lthr), ctypes.byref(nc)),
+           "paper_tables")
+    n = n_off.value
+    return dict(dx=dx[:n], dy=dy[:n], thr=thr[:n], local_thr=lthr.value, n_cand=nc.value)
+
+
+def paper_synapses(p, mode, j0, n):
+    """Synapses of neurons j0..j0+n-1 under the paper law: dict of count[n]
+    and flat arrays (row r's synapses follow those of rows < r, in k order)."""
+    cap = paper_tables(p)["n_cand"]
+    tot = n * cap
+    cnt = np.zeros(n, np.int64)
+    tgt = np.zeros(tot, np.int64)
+    dly = np.zeros(tot, np.int32)
+    wfx = np.zeros(tot, np.int32)
+    w = np.zeros(tot, np.float64)
+    dx = np.zeros(tot, np.int32)
+    dy = np.zeros(tot, np.int32)
+    _check(lib().orc_paper_synapses(ctypes.byref(p), MODES[mode] if isinstance(mode, str) else mode,
+                                    j0, n, cap, _ptr(cnt), _ptr(tgt), _ptr(dly), _ptr(wfx),
+                                    _ptr(w), _ptr(dx), _ptr(dy)), "paper_synapses")
+    keep = (np.arange(cap)[None, :] < cnt[:, None]).ravel()
+    return dict(count=cnt, target=tgt[keep], delay=dly[keep], wfx=wfx[keep], w=w[keep],
+                dx=dx[keep], dy=dy[keep])
 
 
 def ext_counts(p, i0, n, t0, n_steps=None):

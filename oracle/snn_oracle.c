@@ -45,6 +45,9 @@
 #define TAG_EXT 2u
 #define TAG_INIT 3u
 #define TAG_SURR 4u /* normal draws of the relaxed (differentiable) network */
+#define TAG_PCONN 5u /* candidate draws of the paper's connectivity law       */
+#define CONN_FIXED 0
+#define CONN_PAPER 1
 
 #define POIS_CAP 128 /* table entries; lambda is limited so that it saturates */
 #define Q_SIZE 65536
@@ -71,6 +74,11 @@ typedef struct {
   int32_t d_min, d_max;    /* axonal delay range, steps                    */
   double h;                /* step, ms (1 for the network)                 */
   uint64_t seed;
+  int32_t connectivity;    /* CONN_FIXED: the configs' law; CONN_PAPER: Sec. 2 */
+  float p_local;           /* paper: P(synapse) to each other neuron of the column */
+  float remote_a;          /* paper: P at distance r is a exp(-r^2 / 2 sigma^2) */
+  float remote_sigma;      /* paper: sigma, grid steps                      */
+  float remote_cutoff;     /* paper: offsets with P below this are dropped  */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -128,6 +136,10 @@ typedef struct {
   int32_t jx;                     /* external efficacy in 2^-16 mV units     */
   int nref;                       /* refractory steps                        */
   int k_local;                    /* synapses k < k_local stay local         */
+  int n_poff;                     /* paper law: kept remote offsets          */
+  int poff_dx[64], poff_dy[64];   /* dy-major, dx ascending                  */
+  uint64_t poff_thr[64];          /* candidate kept iff its word < thr       */
+  uint64_t plocal_thr;            /* the same for the own column             */
 } orc_tables;
 
 /* Sec. 2: remote connection probability decreases with the distance between
@@ -206,10 +218,35 @@ static double prop_vc(double gc, double tm, double tc, double h, double pvv,
   return -(gc * b) * (pcc - pvv);
 }
 
+/* Sec. 2's own connectivity law (reading): a neuron reaches every other
+ * neuron of its column with probability p_local and every neuron of a column
+ * at Euclidean grid distance r with probability a exp(-r^2 / (2 sigma^2));
+ * offsets where that probability is below the cut-off are dropped (the
+ * paper's "stencil").  Each probability becomes a 32-bit threshold
+ * floor(P 2^32) against one Philox word per candidate. */
+static void make_paper_stencil(const orc_params *p, orc_tables *t) {
+  int dy, dx, n = 0;
+  double s2 = 2.0 * (double)p->remote_sigma * (double)p->remote_sigma;
+  for (dy = -3; dy <= 3; ++dy)
+    for (dx = -3; dx <= 3; ++dx) {
+      double pr;
+      if (dx == 0 && dy == 0) continue;
+      pr = (double)p->remote_a * exp(-(double)(dx * dx + dy * dy) / s2);
+      if (pr < (double)p->remote_cutoff) continue;
+      t->poff_dx[n] = dx;
+      t->poff_dy[n] = dy;
+      t->poff_thr[n] = (uint64_t)floor(pr * 4294967296.0);
+      ++n;
+    }
+  t->n_poff = n;
+  t->plocal_thr = (uint64_t)floor((double)p->p_local * 4294967296.0);
+}
+
 static int make_tables(const orc_params *p, orc_tables *t) {
   double tm = (double)p->tau_m, tc = (double)p->tau_c;
   memset(t, 0, sizeof(*t));
   make_stencil(p, t);
+  make_paper_stencil(p, t);
   make_poisson(p, t);
   t->q = (double *)malloc(sizeof(double) * Q_SIZE);
   if (!t->q) return ORC_ENOMEM;
@@ -240,6 +277,16 @@ static int validate(const orc_params *p) {
   if (!(p->nu_ext_khz >= 0.0f) || (double)p->nu_ext_khz * p->h > 40.0) return ORC_EINVAL;
   if (!(p->lambda_cols > 0.0f)) return ORC_EINVAL;
   if (!(p->frac_local >= 0.0f && p->frac_local <= 1.0f)) return ORC_EINVAL;
+  if (p->connectivity != CONN_FIXED && p->connectivity != CONN_PAPER) return ORC_EINVAL;
+  if (p->connectivity == CONN_PAPER) {
+    double s2 = 2.0 * (double)p->remote_sigma * (double)p->remote_sigma;
+    if (!(p->p_local >= 0.0f && p->p_local <= 1.0f)) return ORC_EINVAL;
+    if (!(p->remote_a >= 0.0f && p->remote_a <= 1.0f)) return ORC_EINVAL;
+    if (!(p->remote_sigma > 0.0f) || !(p->remote_cutoff > 0.0f)) return ORC_EINVAL;
+    /* the kept offsets must fit the 7x7 stencil: the nearest offset outside
+     * it lies at r^2 = 16 */
+    if ((double)p->remote_a * exp(-16.0 / s2) >= (double)p->remote_cutoff) return ORC_EINVAL;
+  }
   return ORC_OK;
 }
 
@@ -267,6 +314,9 @@ typedef struct {
   int32_t dx, dy; /* stencil offset drawn (0,0 for local)        */
 } orc_syn;
 
+static void delay_and_weight(const orc_params *p, const orc_tables *t, int mode, int exc,
+                             const uint32_t x[4], orc_syn *s);
+
 static void synapse(const orc_params *p, const orc_tables *t, int mode,
                     int64_t j, int32_t k, orc_syn *s) {
   uint32_t x[4];
@@ -275,7 +325,6 @@ static void synapse(const orc_params *p, const orc_tables *t, int mode,
   int32_t cx = (int32_t)(col % p->grid_w), cy = (int32_t)(col / p->grid_w);
   int32_t l, tx, ty;
   int exc = lj < p->n_exc;
-  double w;
   draw(p->seed, (uint32_t)j, (uint32_t)k, TAG_CONN, x);
   if (k < t->k_local) {
     l = (int32_t)uniform_below(x[0], (uint32_t)(p->n_per_col - 1));
@@ -294,6 +343,13 @@ static void synapse(const orc_params *p, const orc_tables *t, int mode,
     ty = ((cy + s->dy) % p->grid_h + p->grid_h) % p->grid_h;
   }
   s->target = ((int64_t)ty * p->grid_w + tx) * p->n_per_col + l;
+  delay_and_weight(p, t, mode, exc, x, s);
+}
+
+/* Delay and weight of a synapse from its Philox block x (words 2 and 3). */
+static void delay_and_weight(const orc_params *p, const orc_tables *t, int mode, int exc,
+                             const uint32_t x[4], orc_syn *s) {
+  double w;
   s->delay = p->d_min + (int32_t)uniform_below(x[2], (uint32_t)(p->d_max - p->d_min + 1));
   w = (double)(exc ? p->w_exc : p->w_inh) *
       (1.0 + (double)p->w_cv * t->q[x[3] >> 16]);
@@ -314,6 +370,61 @@ static void synapse(const orc_params *p, const orc_tables *t, int mode,
     s->w = w;
     s->wfx = 0;
   }
+}
+
+/* Candidates of neuron j under the paper's law, in a fixed order: the other
+ * n_per_col - 1 neurons of its own column (ascending index), then for each
+ * kept remote offset (dy-major, dx ascending) the n_per_col neurons of that
+ * column.  Candidate c is kept iff word c mod 4 of Philox(seed; j, c / 4,
+ * PCONN) is below its threshold.  The k-th kept candidate (k from 0) is
+ * synapse k: its delay and weight come from Philox(seed; j, k, CONN) as in
+ * the fixed law.  Writes the synapses to out (capacity: the candidate count)
+ * and returns how many there are. */
+static int64_t paper_row(const orc_params *p, const orc_tables *t, int mode, int64_t j,
+                         orc_syn *out) {
+  const int32_t npc = p->n_per_col;
+  int64_t col = j / npc;
+  int32_t lj = (int32_t)(j % npc);
+  int32_t cx = (int32_t)(col % p->grid_w), cy = (int32_t)(col / p->grid_w);
+  int exc = lj < p->n_exc;
+  int64_t n_cand = (int64_t)(npc - 1) + (int64_t)t->n_poff * npc, c, k = 0;
+  uint32_t word[4];
+  for (c = 0; c < n_cand; ++c) {
+    uint64_t thr;
+    int32_t l, tx, ty, dx, dy;
+    if ((c & 3) == 0) draw(p->seed, (uint32_t)j, (uint32_t)(c >> 2), TAG_PCONN, word);
+    if (c < npc - 1) {
+      thr = t->plocal_thr;
+      l = (int32_t)c + ((int32_t)c >= lj ? 1 : 0);
+      dx = 0;
+      dy = 0;
+    } else {
+      int64_t r = c - (npc - 1);
+      int m = (int)(r / npc);
+      thr = t->poff_thr[m];
+      l = (int32_t)(r % npc);
+      dx = t->poff_dx[m];
+      dy = t->poff_dy[m];
+    }
+    if ((uint64_t)word[c & 3] >= thr) continue;
+    tx = ((cx + dx) % p->grid_w + p->grid_w) % p->grid_w;
+    ty = ((cy + dy) % p->grid_h + p->grid_h) % p->grid_h;
+    {
+      uint32_t x[4];
+      orc_syn *s = &out[k];
+      s->target = ((int64_t)ty * p->grid_w + tx) * npc + l;
+      s->dx = dx;
+      s->dy = dy;
+      draw(p->seed, (uint32_t)j, (uint32_t)k, TAG_CONN, x);
+      delay_and_weight(p, t, mode, exc, x, s);
+    }
+    ++k;
+  }
+  return k;
+}
+
+static int64_t paper_candidates(const orc_params *p, const orc_tables *t) {
+  return (int64_t)(p->n_per_col - 1) + (int64_t)t->n_poff * p->n_per_col;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -442,6 +553,7 @@ int orc_synapses(const orc_params *p, int mode, int64_t j0, int64_t n,
   if (rc) return rc;
   N = (int64_t)p->grid_w * p->grid_h * p->n_per_col;
   if (j0 < 0 || n < 0 || j0 + n > N) return ORC_EINVAL;
+  if (p->connectivity != CONN_FIXED) return ORC_EINVAL; /* see orc_paper_synapses */
   rc = make_tables(p, &t);
   if (rc) return rc;
   for (j = j0; j < j0 + n; ++j)
@@ -455,6 +567,67 @@ int orc_synapses(const orc_params *p, int mode, int64_t j0, int64_t n,
       if (dx) dx[o] = s.dx;
       if (dy) dy[o] = s.dy;
     }
+  free_tables(&t);
+  return ORC_OK;
+}
+
+/* The paper law's kept offsets and thresholds (n_off <= 48). */
+int orc_paper_tables(const orc_params *p, int32_t *n_off, int32_t *dx, int32_t *dy,
+                     uint64_t *thr, uint64_t *local_thr, int64_t *n_cand) {
+  orc_tables t;
+  int m, rc = validate(p);
+  if (rc) return rc;
+  rc = make_tables(p, &t);
+  if (rc) return rc;
+  *n_off = t.n_poff;
+  for (m = 0; m < t.n_poff; ++m) {
+    dx[m] = t.poff_dx[m];
+    dy[m] = t.poff_dy[m];
+    thr[m] = t.poff_thr[m];
+  }
+  *local_thr = t.plocal_thr;
+  *n_cand = paper_candidates(p, &t);
+  free_tables(&t);
+  return ORC_OK;
+}
+
+/* Synapses of neurons j0 .. j0+n-1 under the paper law: row r's count[r]
+ * synapses at [r * cap, r * cap + count[r]) of each array (cap >= the
+ * candidate count), in k order. */
+int orc_paper_synapses(const orc_params *p, int mode, int64_t j0, int64_t n, int64_t cap,
+                       int64_t *count, int64_t *target, int32_t *delay, int32_t *wfx,
+                       double *w, int32_t *dx, int32_t *dy) {
+  orc_tables t;
+  orc_syn *row;
+  int64_t N, r, k;
+  int rc = validate(p);
+  if (rc) return rc;
+  N = (int64_t)p->grid_w * p->grid_h * p->n_per_col;
+  if (p->connectivity != CONN_PAPER || j0 < 0 || n < 0 || j0 + n > N) return ORC_EINVAL;
+  rc = make_tables(p, &t);
+  if (rc) return rc;
+  if (cap < paper_candidates(p, &t)) {
+    free_tables(&t);
+    return ORC_EINVAL;
+  }
+  row = (orc_syn *)malloc(sizeof(orc_syn) * (size_t)paper_candidates(p, &t));
+  if (!row) {
+    free_tables(&t);
+    return ORC_ENOMEM;
+  }
+  for (r = 0; r < n; ++r) {
+    int64_t cnt = paper_row(p, &t, mode, j0 + r, row), o = r * cap;
+    count[r] = cnt;
+    for (k = 0; k < cnt; ++k, ++o) {
+      if (target) target[o] = row[k].target;
+      if (delay) delay[o] = row[k].delay;
+      if (wfx) wfx[o] = row[k].wfx;
+      if (w) w[o] = row[k].w;
+      if (dx) dx[o] = row[k].dx;
+      if (dy) dy[o] = row[k].dy;
+    }
+  }
+  free(row);
   free_tables(&t);
   return ORC_OK;
 }
@@ -569,12 +742,17 @@ int orc_run(const orc_params *p, int mode, int64_t n_steps, int64_t cap,
   double *R64 = NULL, *V64 = NULL, *C64 = NULL;
   float *V32 = NULL, *C32 = NULL;
   uint8_t *ref = NULL;
+  orc_syn *prow = NULL; /* paper law: one row's synapses */
   float pvv32, pcc32, pvc32[2];
   if (rc) return rc;
   rc = make_tables(p, &tb);
   if (rc) return rc;
   N = (int64_t)p->grid_w * p->grid_h * p->n_per_col;
   DR = p->d_max + 1;
+  if (p->connectivity == CONN_PAPER) {
+    prow = (orc_syn *)malloc(sizeof(orc_syn) * (size_t)paper_candidates(p, &tb));
+    if (!prow) rc = ORC_ENOMEM;
+  }
   ref = (uint8_t *)calloc((size_t)N, 1);
   fired = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
   if (mode == ORC_MODE_F64) {
@@ -626,13 +804,17 @@ int orc_run(const orc_params *p, int mode, int64_t n_steps, int64_t cap,
       }
       if (spk) fired[nf++] = (int32_t)i;
     }
-    /* every spike travels through its k_out synapses into slot t + d */
+    /* every spike travels through its synapses into slot t + d */
     for (i = 0; i < nf; ++i) {
-      int32_t k;
-      for (k = 0; k < p->k_out; ++k) {
+      int64_t k, cnt = p->k_out;
+      if (prow) cnt = paper_row(p, &tb, mode, fired[i], prow);
+      for (k = 0; k < cnt; ++k) {
         orc_syn s;
         int ds;
-        synapse(p, &tb, mode, fired[i], k, &s);
+        if (prow)
+          s = prow[k];
+        else
+          synapse(p, &tb, mode, fired[i], (int32_t)k, &s);
         ds = (int)((t + s.delay) % DR);
         if (mode == ORC_MODE_F64)
           R64[(size_t)ds * N + s.target] += s.w;
@@ -656,7 +838,7 @@ int orc_run(const orc_params *p, int mode, int64_t n_steps, int64_t cap,
   }
 done:
   free(R32); free(R64); free(V32); free(V64); free(C32); free(C64);
-  free(ref); free(fired);
+  free(ref); free(fired); free(prow);
   free_tables(&tb);
   return rc;
 }

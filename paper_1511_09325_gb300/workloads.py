@@ -44,6 +44,14 @@ SYNAPSE = dict(
     d_min=1,
     d_max=20,
     periodic=1,
+    # 0: the law above; 1: Sec. 2's own law (Bernoulli p_local inside the
+    # column, remote_a exp(-r^2 / 2 remote_sigma^2) to each neuron of a column
+    # at distance r, offsets below remote_cutoff dropped; variable out-degree)
+    connectivity=0,
+    p_local=0.8,
+    remote_a=0.05,
+    remote_sigma=1.0,
+    remote_cutoff=0.001,
 )
 
 # Named workloads.  "steps" is the simulated length in 1 ms steps.

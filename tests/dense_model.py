@@ -45,10 +45,14 @@ class DenseNet:
         self.p, self.mode = p, mode
         N = p.grid_w * p.grid_h * p.n_per_col
         self.N = N
-        syn = orc.synapses(p, mode, 0, N)
+        if p.connectivity == 1:   # the paper's law: variable out-degree
+            syn = orc.paper_synapses(p, mode, 0, N)
+            src = np.repeat(np.arange(N), syn["count"])
+        else:
+            syn = orc.synapses(p, mode, 0, N)
+            src = np.repeat(np.arange(N), p.k_out)
         self.tb = orc.tables(p)
         self.D = p.d_max
-        src = np.repeat(np.arange(N), p.k_out)
         self.A = []
         for d in range(1, self.D + 1):
             m = syn["delay"].ravel() == d
