@@ -134,7 +134,7 @@ def _cpu_baseline(workload, seconds_target=15.0):
     import oracle
 
     cfg = W.WORKLOADS[workload]
-    n, s = W.neuron_params(), W.synapse_params()
+    n, s = W.neuron_params(), W.synapse_params(**cfg.get("synapse", {}))
     p = oracle.make_params(cfg["grid_w"], cfg["grid_h"], n, s, cfg["seed"])
     mode = cfg["precision"]
     oracle.build()
@@ -184,7 +184,7 @@ def reduce_ranks(dist, ms, rec_ev, ext_ev, device):
 
 
 def _build_net(snn, torch, cfg, seed, stream):
-    n, s = W.neuron_params(), W.synapse_params()
+    n, s = W.neuron_params(), W.synapse_params(**cfg.get("synapse", {}))
     t0 = time.perf_counter()
     net = snn.Net(cfg["grid_w"], cfg["grid_h"], n, s, seed, cfg["precision"],
                   stream=stream.cuda_stream)
@@ -302,11 +302,12 @@ def run_ours(args):
     P = K if args.profile_steps is None else min(args.profile_steps, K)
     roofline = _kernel_roofline(snn, torch, cfg, seed, stream, Wm, max(1, P), args.workload)
 
-    extra = batched = surrogate = None
+    extra = batched = surrogate = paper = None
     if not args.no_extra and ws == 1:
         extra = _precision_form(snn, torch, stream, Wm)
         batched = _batched_form(snn, torch, stream)
         surrogate = _surrogate_form(snn, torch, stream)
+        paper = _paper_form(snn, torch, stream, Wm)
     cpu = None
     if ws == 1 and not args.no_cpu:
         cb = _cpu_baseline(args.workload)
@@ -343,6 +344,8 @@ def run_ours(args):
             line["batched_form"] = batched
         if surrogate:
             line["surrogate_gradient"] = surrogate
+        if paper:
+            line["paper_connectivity"] = paper
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -449,6 +452,27 @@ def _precision_form(snn, torch, stream, warmup, steps=1000):
     if "events_per_s" in out.get("f16w", {}) and "events_per_s" in out.get("f32w", {}):
         out["fp16_speedup_wall"] = out["f32w"]["ms_per_step"] / out["f16w"]["ms_per_step"]
     return out
+
+
+def _paper_form(snn, torch, stream, warmup, steps=2000):
+    """24x24 columns under the paper's own connectivity law (Bernoulli local,
+    Gaussian remote, variable out-degree): same metric, same timing."""
+    cfg = W.WORKLOADS["cols24x24_paper_f32w"]
+    net, build_s = _build_net(snn, torch, cfg, cfg["seed"], stream)
+    info = net.info()
+    net.step(warmup)
+    net.spikes()
+    ms, rec_ev, _ = _timed(net, torch, stream, steps)
+    _, pop = net.rates()
+    kms, kb = net.step_profiled(min(steps, 500))
+    net.close()
+    torch.cuda.empty_cache()
+    return {"workload": "cols24x24_paper_f32w", "steps": steps, "warmup": warmup,
+            "synapses": info["synapses"], "build_s": build_s,
+            "events_per_s": rec_ev / (ms * 1e-3), "ms_per_step": ms / steps,
+            "pop_rates_hz": [float(pop[0]), float(pop[1])],
+            "deliver_gbs": kb[1] / (kms[1] * 1e-3) / 1e9,
+            "update_gbs": kb[0] / (kms[0] * 1e-3) / 1e9}
 
 
 def main():

@@ -60,7 +60,20 @@ typedef struct {
   float nu_ext_kHz;  /* external Poisson rate per neuron (2.5 kHz)         */
 } snn_neuron_params;
 
-/* Connectivity (Sec. 2: local plus distance-dependent remote synapses). */
+/* Connectivity (Sec. 2: local plus distance-dependent remote synapses).
+ * Two laws:
+ *   SNN_CONN_FIXED: exactly k_out synapses per neuron; the first
+ *     round(frac_local k_out) go to other neurons of the own column, the rest
+ *     to columns of the (2 radius + 1)^2 stencil with P ~ exp(-r / lambda);
+ *   SNN_CONN_PAPER: the law stated in Sec. 2: a synapse to every other neuron
+ *     of the own column with probability p_local, and to every neuron of a
+ *     column at Euclidean grid distance r with probability
+ *     remote_a exp(-r^2 / (2 remote_sigma^2)), offsets where that is below
+ *     remote_cutoff being dropped (they must all lie within the 7x7
+ *     stencil); the out-degree varies from neuron to neuron (k_out,
+ *     frac_local, lambda_cols and stencil_radius are then unused).
+ * Delays and weights follow the same rules under both laws. */
+enum { SNN_CONN_FIXED = 0, SNN_CONN_PAPER = 1 };
 typedef struct {
   int32_t k_out;          /* outgoing synapses per neuron (1240)            */
   float frac_local;       /* fraction inside the own column (0.5)           */
@@ -71,6 +84,11 @@ typedef struct {
   float w_cv;             /* coefficient of variation of weights (0.25)     */
   int32_t d_min, d_max;   /* axonal delays, whole steps, 1 <= d_min <= d_max <= 32 */
   int32_t periodic;       /* must be 1: the grid is a torus                  */
+  int32_t connectivity;   /* SNN_CONN_FIXED or SNN_CONN_PAPER               */
+  float p_local;          /* paper law: own-column probability (0.8)        */
+  float remote_a;         /* paper law: amplitude of the remote law (0.05)  */
+  float remote_sigma;     /* paper law: its width, grid steps (1)           */
+  float remote_cutoff;    /* paper law: smallest kept probability (0.001)   */
 } snn_synapse_params;
 
 enum {
@@ -153,11 +171,16 @@ int snn_get_state(snn_net* net, float* v, float* c, uint8_t* refractory);
 
 /*
  * snn_read_synapses -- decode the outgoing synapses of neurons j0..j0+n-1 from
- * the device table into host arrays of n * k_out entries, grouped by neuron,
+ * the device table into host arrays, grouped by neuron (neuron j0's first),
  * within a neuron by delay: target neuron, delay (steps), weight in 2^-16 mV.
+ * The arrays hold the sum of the rows' lengths (snn_row_lengths): n * k_out
+ * entries under SNN_CONN_FIXED.
  */
 int snn_read_synapses(snn_net* net, int64_t j0, int64_t n, int64_t* target,
                       int32_t* delay, int32_t* wfx);
+
+/* snn_row_lengths -- counts[r] = outgoing synapses of neuron j0 + r, r < n. */
+int snn_row_lengths(snn_net* net, int64_t j0, int64_t n, int32_t* counts);
 
 /*
  * snn_info -- sizes of the net: info[0] = N neurons, [1] = synapses,

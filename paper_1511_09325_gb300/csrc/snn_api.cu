@@ -34,6 +34,10 @@ struct snn_net {
   uint32_t* ids = nullptr;
   unsigned* cnt = nullptr;
   unsigned* ccnt = nullptr;
+  uint32_t* deg = nullptr;                 // out-degree per neuron (paper law)
+  unsigned long long* syn_part = nullptr;  // synaptic events per update block
+  long long total_syn = 0;                 // synapses of the whole net
+  int connectivity = SNN_CONN_FIXED;
   unsigned* isum = nullptr;
   unsigned* gsum = nullptr;
   Ctl* ctl = nullptr;
@@ -142,7 +146,7 @@ void release(snn_net* net) {
   if (net->hmap) cudaFreeHost(net->hmap);
   if (net->hstage) cudaFreeHost(net->hstage);
   void* ptrs[] = {net->syn, net->bend, net->V, net->C, net->R, net->acc,
-                  net->ids, net->cnt, net->ccnt, net->isum, net->gsum, net->ctl, net->rec, net->rcnt, net->stage, net->rpre, net->dhdr, net->colcnt,
+                  net->ids, net->cnt, net->ccnt, net->deg, net->syn_part, net->isum, net->gsum, net->ctl, net->rec, net->rcnt, net->stage, net->rpre, net->dhdr, net->colcnt,
                   net->ext_part, net->spk_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -171,8 +175,19 @@ int validate(int gw, int gh, const snn_neuron_params* n, const snn_synapse_param
     return bad("non-finite weight parameter");
   if (precision != SNN_EXACT_F32W && precision != SNN_EXACT_F16W) return bad("unknown precision");
   const int ndel = s->d_max - s->d_min + 1;
-  if ((s->k_out + (kSlotUnit - 1) * ndel + kSlotUnit - 1) / kSlotUnit > 255)
+  if (s->connectivity != SNN_CONN_FIXED && s->connectivity != SNN_CONN_PAPER)
+    return bad("connectivity must be SNN_CONN_FIXED or SNN_CONN_PAPER");
+  if (s->connectivity == SNN_CONN_FIXED &&
+      (s->k_out + (kSlotUnit - 1) * ndel + kSlotUnit - 1) / kSlotUnit > 255)
     return bad("k_out too large for 8-bit bucket ends");
+  if (s->connectivity == SNN_CONN_PAPER &&
+      (!(s->p_local >= 0.f && s->p_local <= 1.f) || !(s->remote_a >= 0.f && s->remote_a <= 1.f) ||
+       !(s->remote_sigma > 0.f) || !std::isfinite(s->remote_sigma) || !(s->remote_cutoff > 0.f)))
+    return bad("paper law: p_local and remote_a in [0, 1], remote_sigma and remote_cutoff > 0");
+  if (s->connectivity == SNN_CONN_PAPER &&
+      (double)s->remote_a * std::exp(-16.0 / (2.0 * (double)s->remote_sigma * s->remote_sigma)) >=
+          (double)s->remote_cutoff)
+    return bad("the paper law keeps offsets beyond the 7x7 stencil");
   const long long N = (long long)gw * gh * n->n_per_col;
   if (N >= (1LL << 31) - 4) return bad("too many neurons");
   return SNN_OK;
@@ -231,6 +246,8 @@ void fill_step_params(snn_net* net) {
   p.ids = net->ids;
   p.cnt = net->cnt;
   p.ccnt = net->ccnt;
+  p.deg = net->deg;
+  p.syn_part = net->syn_part;
   p.isum = net->isum;
   p.gsum = net->gsum;
   p.bend = net->bend;
@@ -279,9 +296,62 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   net->deliver_grid = deliver_grid(precision, net->num_sms, net->npc, net->agg);
   net->rec_region = (net->rec_cap + net->update_grid - 1) / net->update_grid;
 
+  net->connectivity = sp->connectivity;
+  BuildParams bp{};
+  bp.N = net->N;
+  bp.npc = net->npc;
+  bp.nexc = net->nexc;
+  bp.W = net->W;
+  bp.H = net->H;
+  bp.K = net->K;
+  bp.k_local = net->tables.k_local;
+  bp.dmin = net->dmin;
+  bp.ndel = net->ndel;
+  bp.n_off = net->tables.n_off;
+  bp.seed_lo = (uint32_t)(seed & 0xFFFFFFFFu);
+  bp.seed_hi = (uint32_t)(seed >> 32);
+  std::memcpy(bp.stencil_thr, net->tables.stencil_thr, sizeof(bp.stencil_thr));
+  std::memcpy(bp.off_dx, net->tables.off_dx, sizeof(bp.off_dx));
+  std::memcpy(bp.off_dy, net->tables.off_dy, sizeof(bp.off_dy));
+  bp.n_poff = net->tables.n_poff;
+  bp.n_cand = net->tables.n_cand;
+  std::memcpy(bp.poff_thr, net->tables.poff_thr, sizeof(bp.poff_thr));
+  bp.plocal_thr = net->tables.plocal_thr;
+  std::memcpy(bp.poff_dx, net->tables.poff_dx, sizeof(bp.poff_dx));
+  std::memcpy(bp.poff_dy, net->tables.poff_dy, sizeof(bp.poff_dy));
+  if ((rc = dalloc(net, &net->bend, (size_t)net->N * kBendStride))) return rc;
+  net->total_syn = net->N * (long long)net->K;
+  if (net->connectivity == SNN_CONN_PAPER) {
+    // count pass: bucket ends, out-degrees and the longest row, which sets
+    // the row stride of the table
+    unsigned* dmax = nullptr;
+    if ((rc = dalloc(net, &net->deg, (size_t)net->N * 4))) return rc;
+    if ((rc = dalloc(net, &dmax, 4))) return rc;
+    net->device_bytes -= 4;
+    unsigned max_units = 0u;
+    bp.bend = net->bend;
+    bp.deg = net->deg;
+    bp.max_units = dmax;
+    cudaError_t ce = cudaMemsetAsync(dmax, 0, 4, net->stream);
+    if (ce == cudaSuccess) ce = launch_paper_count(bp, net->num_sms, net->stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(&max_units, dmax, 4, cudaMemcpyDeviceToHost, net->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(net->stream);
+    cudaFree(dmax);
+    if (ce != cudaSuccess) return cuda_fail(net, ce, "connectivity count pass");
+    if (max_units > 255u)
+      return fail(net, SNN_EINVAL, "a row of the paper law needs more than 2040 slots");
+    net->rowcap = (int)std::max(1u, max_units) * kSlotUnit;
+    std::vector<uint32_t> deg((size_t)net->N);
+    SNN_CUDA(net, cudaMemcpyAsync(deg.data(), net->deg, deg.size() * 4, cudaMemcpyDeviceToHost,
+                                  net->stream));
+    SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+    net->total_syn = 0;
+    for (uint32_t d : deg) net->total_syn += d;
+  }
+  bp.rowcap = net->rowcap;
   const size_t syn_bytes = (size_t)net->N * net->rowcap * net->rec_size;
   if ((rc = dalloc(net, &net->syn, syn_bytes))) return rc;
-  if ((rc = dalloc(net, &net->bend, (size_t)net->N * kBendStride))) return rc;
   if ((rc = dalloc(net, &net->V, (size_t)net->Npad * 4))) return rc;
   if ((rc = dalloc(net, &net->C, (size_t)net->Npad * 4))) return rc;
   if ((rc = dalloc(net, &net->R, (size_t)net->Npad))) return rc;
@@ -305,6 +375,7 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if ((rc = dalloc(net, &net->colcnt, (size_t)net->ncol * 2 * 8))) return rc;
   if ((rc = dalloc(net, &net->ext_part, (size_t)net->update_grid * 8))) return rc;
   if ((rc = dalloc(net, &net->spk_part, (size_t)net->update_grid * 8))) return rc;
+  if ((rc = dalloc(net, &net->syn_part, (size_t)net->update_grid * 8))) return rc;
   uint32_t* wtab = nullptr;
   if ((rc = dalloc(net, &wtab, net->tables.wtab.size() * 4))) return rc;
   net->device_bytes -= net->tables.wtab.size() * 4;
@@ -322,29 +393,15 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if (e == cudaSuccess) e = cudaMemsetAsync(net->colcnt, 0, (size_t)net->ncol * 16, net->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(net->ext_part, 0, (size_t)net->update_grid * 8, net->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(net->spk_part, 0, (size_t)net->update_grid * 8, net->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(net->syn_part, 0, (size_t)net->update_grid * 8, net->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(net->rcnt, 0, (size_t)net->update_grid * 8, net->stream);
   if (e == cudaSuccess) {
-    BuildParams bp{};
-    bp.N = net->N;
-    bp.npc = net->npc;
-    bp.nexc = net->nexc;
-    bp.W = net->W;
-    bp.H = net->H;
-    bp.K = net->K;
-    bp.k_local = net->tables.k_local;
-    bp.dmin = net->dmin;
-    bp.ndel = net->ndel;
-    bp.rowcap = net->rowcap;
-    bp.n_off = net->tables.n_off;
-    bp.seed_lo = (uint32_t)(seed & 0xFFFFFFFFu);
-    bp.seed_hi = (uint32_t)(seed >> 32);
-    std::memcpy(bp.stencil_thr, net->tables.stencil_thr, sizeof(bp.stencil_thr));
-    std::memcpy(bp.off_dx, net->tables.off_dx, sizeof(bp.off_dx));
-    std::memcpy(bp.off_dy, net->tables.off_dy, sizeof(bp.off_dy));
     bp.wtab = wtab;
     bp.syn = net->syn;
     bp.bend = net->bend;
-    e = launch_build(bp, precision, net->num_sms, net->stream);
+    bp.deg = net->deg;
+    e = net->connectivity == SNN_CONN_PAPER ? launch_paper_fill(bp, precision, net->num_sms, net->stream)
+                                            : launch_build(bp, precision, net->num_sms, net->stream);
   }
   fill_step_params(net);
   if (e == cudaSuccess) e = launch_init_state(net->sp, net->stream);
@@ -481,7 +538,7 @@ int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes) 
       t_dl += b;
       const double S = (double)(hspk[s + 1] - hspk[s]);
       b_up += neuron_bytes + 12.0 * S;
-      b_dl += S * ((double)net->K * net->rec_size + 6.0 * net->ndel);
+      b_dl += S * ((double)net->total_syn / (double)net->N * net->rec_size + 6.0 * net->ndel);
     }
   } else {
     rc = cuda_fail(net, e, "profiled step");
@@ -671,18 +728,19 @@ int snn_stats(snn_net* net, double* recurrent_events, double* external_events, i
   cudaError_t e;
   Ctl c = read_ctl(net, &e);
   if (e != cudaSuccess) return cuda_fail(net, e, "read control block");
-  std::vector<unsigned long long> ext((size_t)net->update_grid), spk((size_t)net->update_grid);
+  std::vector<unsigned long long> ext((size_t)net->update_grid), syn((size_t)net->update_grid);
   SNN_CUDA(net, cudaMemcpyAsync(ext.data(), net->ext_part, ext.size() * 8, cudaMemcpyDeviceToHost,
                                 net->stream));
-  SNN_CUDA(net, cudaMemcpyAsync(spk.data(), net->spk_part, spk.size() * 8, cudaMemcpyDeviceToHost,
+  SNN_CUDA(net, cudaMemcpyAsync(syn.data(), net->syn_part, syn.size() * 8, cudaMemcpyDeviceToHost,
                                 net->stream));
   SNN_CUDA(net, cudaStreamSynchronize(net->stream));
-  unsigned long long se = 0ull, ss = 0ull;
+  unsigned long long se = 0ull, sy = 0ull;
   for (size_t b = 0; b < ext.size(); ++b) {
     se += ext[b];
-    ss += spk[b];
+    sy += syn[b];
   }
-  if (recurrent_events) *recurrent_events = (double)ss * (double)net->K;
+  // every spike counts its neuron's out-degree (k_out under the fixed law)
+  if (recurrent_events) *recurrent_events = (double)sy;
   if (external_events) *external_events = (double)se;
   if (steps) *steps = (int64_t)c.t;
   return SNN_OK;
@@ -712,6 +770,11 @@ int snn_read_synapses(snn_net* net, int64_t j0, int64_t n, int64_t* target, int3
                                 cudaMemcpyDeviceToHost, net->stream));
   int rc = sync(net);
   if (rc) return rc;
+  std::vector<int32_t> len((size_t)n);
+  rc = snn_row_lengths(net, j0, n, len.data());
+  if (rc) return rc;
+  long long total = 0;
+  for (int32_t v : len) total += v;
   long long o = 0;
   for (int64_t r = 0; r < n; ++r) {
     const long long j = j0 + r;
@@ -740,7 +803,7 @@ int snn_read_synapses(snn_net* net, int64_t j0, int64_t n, int64_t* target, int3
           if (code == kPad) continue;
           w = (int32_t)wbits;
         }
-        if (o >= (long long)n * net->K) return fail(net, SNN_ESTATE, "row holds too many synapses");
+        if (o >= total) return fail(net, SNN_ESTATE, "row holds too many synapses");
         if (net->precision == SNN_EXACT_F16W) {
           const int dy = (int)((code >> 14) & 7u) - 3, dx = (int)((code >> 11) & 7u) - 3;
           const int ty = ((cy + dy) % net->H + net->H) % net->H;
@@ -756,13 +819,26 @@ int snn_read_synapses(snn_net* net, int64_t j0, int64_t n, int64_t* target, int3
       beg = end;
     }
   }
-  if (o != (long long)n * net->K) return fail(net, SNN_ESTATE, "row holds too few synapses");
+  if (o != total) return fail(net, SNN_ESTATE, "row holds too few synapses");
   return SNN_OK;
+}
+
+int snn_row_lengths(snn_net* net, int64_t j0, int64_t n, int32_t* counts) {
+  if (!net || j0 < 0 || n < 0 || j0 + n > net->N || (n > 0 && !counts))
+    return fail(net, SNN_EINVAL, "bad argument");
+  if (n == 0) return SNN_OK;
+  if (!net->deg) {
+    for (int64_t r = 0; r < n; ++r) counts[r] = net->K;
+    return SNN_OK;
+  }
+  SNN_CUDA(net, cudaMemcpyAsync(counts, net->deg + j0, (size_t)n * 4, cudaMemcpyDeviceToHost,
+                                net->stream));
+  return sync(net);
 }
 
 int snn_info(snn_net* net, int64_t* info, int n) {
   if (!net || !info) return fail(net, SNN_EINVAL, "null argument");
-  const int64_t v[6] = {net->N, net->N * (int64_t)net->K, (int64_t)net->device_bytes,
+  const int64_t v[6] = {net->N, (int64_t)net->total_syn, (int64_t)net->device_bytes,
                         net->N * (int64_t)net->rowcap * net->rec_size, net->rowcap,
                         net->precision};
   for (int i = 0; i < n && i < 6; ++i) info[i] = v[i];

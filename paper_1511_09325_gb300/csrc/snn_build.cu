@@ -141,7 +141,161 @@ __global__ void __launch_bounds__(256) init_state_kernel(const StepParams P) {
   reinterpret_cast<uchar4*>(P.R)[q] = make_uchar4(0, 0, 0, 0);
 }
 
+// Paper connectivity law (Sec. 2): candidate c of neuron j -- the column's
+// other neurons in ascending order, then the n_per_col neurons of each kept
+// remote offset -- is kept iff word c mod 4 of Philox(j, c / 4, PCONN) is
+// below its threshold.  The k-th kept candidate is synapse k, whose delay and
+// weight come from Philox(j, k, CONN) as under the fixed law.  One warp per
+// row; in pass it, lane e takes candidates 128 it + 4 e .. + 3, so a warp
+// scan of the lanes' kept counts ranks them.  The count pass (FILL false)
+// writes the bucket ends, the out-degree and the largest row; the fill pass
+// makes the same draws and places every synapse (warp match + popc rank, as
+// in build_rows_kernel), then pads the buckets.
+template <int PREC, bool FILL>
+__global__ void __launch_bounds__(kBuildWarps * 32) paper_rows_kernel(const BuildParams P) {
+  __shared__ unsigned s_cnt[kBuildWarps][32];
+  __shared__ unsigned s_cur[kBuildWarps][32];
+  __shared__ unsigned long long s_thr[kMaxOff];
+  __shared__ int s_dx[kMaxOff], s_dy[kMaxOff];
+  for (int m = threadIdx.x; m < kMaxOff; m += blockDim.x) {
+    s_thr[m] = m < P.n_poff ? P.poff_thr[m] : 0ull;
+    s_dx[m] = m < P.n_poff ? P.poff_dx[m] : 0;
+    s_dy[m] = m < P.n_poff ? P.poff_dy[m] : 0;
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * kBuildWarps;
+  const uint32_t ndel = (uint32_t)P.ndel;
+  const unsigned lt_mask = (1u << lane) - 1u;
+
+  for (long long j = (long long)blockIdx.x * kBuildWarps + w; j < P.N; j += nwarps) {
+    const uint32_t jj = (uint32_t)j;
+    const int col = (int)(j / P.npc);
+    const int lj = (int)(j - (long long)col * P.npc);
+    const int cy = col / P.W, cx = col - cy * P.W;
+    const uint32_t* wt = P.wtab + (lj < P.nexc ? 0 : 65536);
+    const long long row = j * (long long)P.rowcap;
+    if (FILL)
+      s_cur[w][lane] = lane < P.ndel ? (lane ? (unsigned)P.bend[j * kBendStride + lane - 1] : 0u) * kSlotUnit : 0u;
+    else
+      s_cnt[w][lane] = 0u;
+    __syncwarp();
+    unsigned k_run = 0u;
+    for (long long c0 = 0; c0 < P.n_cand; c0 += 128) {
+      const long long cb = c0 + 4 * lane;
+      const uint4 x = philox4x32_10(make_uint4(jj, (uint32_t)(cb >> 2), kTagPConn, 0u), P.seed_lo,
+                                    P.seed_hi);
+      const uint32_t words[4] = {x.x, x.y, x.z, x.w};
+      unsigned bits = 0u;
+      int lq[4], mq[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long c = cb + q;
+        lq[q] = 0;
+        mq[q] = -1;
+        if (c >= P.n_cand) continue;
+        unsigned long long thr;
+        if (c < P.npc - 1) {
+          thr = P.plocal_thr;
+          lq[q] = (int)c + ((int)c >= lj ? 1 : 0);
+        } else {
+          const long long r = c - (P.npc - 1);
+          const int m = (int)(r / P.npc);
+          thr = s_thr[m];
+          mq[q] = m;
+          lq[q] = (int)(r - (long long)m * P.npc);
+        }
+        if ((unsigned long long)words[q] < thr) bits |= 1u << q;
+      }
+      const unsigned nb = (unsigned)__popc(bits);
+      unsigned incl = nb;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const unsigned kb = k_run + incl - nb;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool keep = (bits >> q) & 1u;
+        int b = 63;
+        uint32_t code = 0u, wbits = 0u;
+        if (keep) {
+          const unsigned k = kb + (unsigned)__popc(bits & ((1u << q) - 1u));
+          const uint4 y = philox4x32_10(make_uint4(jj, k, kTagConn, 0u), P.seed_lo, P.seed_hi);
+          b = (int)below(y.z, ndel);
+          if (FILL) wbits = wt[y.w >> 16];
+          const int m = mq[q];
+          const int dx = m < 0 ? 0 : s_dx[m], dy = m < 0 ? 0 : s_dy[m];
+          if (PREC == SNN_EXACT_F16W) {
+            code = ((uint32_t)(((dy + 3) << 3) | (dx + 3)) << 11) | (uint32_t)lq[q];
+          } else {
+            const int ty = wrap(cy + dy, P.H), tx = wrap(cx + dx, P.W);
+            code = ((uint32_t)ty * (uint32_t)P.W + (uint32_t)tx) * (uint32_t)P.npc + (uint32_t)lq[q];
+          }
+        }
+        if (!FILL) {
+          if (keep) atomicAdd(&s_cnt[w][b], 1u);
+        } else {
+          const unsigned peers = __match_any_sync(0xFFFFFFFFu, b);
+          const unsigned rank = __popc(peers & lt_mask);
+          const unsigned pos = s_cur[w][b & 31] + rank;
+          __syncwarp();
+          if (keep) {
+            if (PREC == SNN_EXACT_F16W) {
+              static_cast<uint32_t*>(P.syn)[row + pos] = ((wbits & 0x7FFFu) << 17) | code;
+            } else {
+              const int32_t wfx = __float2int_rn(__fmul_rn(__uint_as_float(wbits), 65536.0f));
+              static_cast<uint2*>(P.syn)[row + pos] = make_uint2(code, (uint32_t)wfx);
+            }
+            if (rank == 0) s_cur[w][b] += __popc(peers);
+          }
+          __syncwarp();
+        }
+      }
+      k_run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+    __syncwarp();
+    if (!FILL) {
+      const unsigned units = lane < P.ndel ? (s_cnt[w][lane] + (kSlotUnit - 1)) / kSlotUnit : 0u;
+      unsigned incl = units;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      P.bend[j * kBendStride + lane] = (uint8_t)(lane < P.ndel ? (incl < 255u ? incl : 255u) : 0u);
+      if (lane == 31) atomicMax(P.max_units, incl);
+      if (lane == 0) P.deg[j] = k_run;
+    } else if (lane < P.ndel) {
+      const unsigned end = (unsigned)P.bend[j * kBendStride + lane] * kSlotUnit;
+      for (unsigned s = s_cur[w][lane]; s < end; ++s) {
+        if (PREC == SNN_EXACT_F16W)
+          static_cast<uint32_t*>(P.syn)[row + s] = kPad;
+        else
+          static_cast<uint2*>(P.syn)[row + s] = make_uint2(kPad, 0u);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_paper_count(const BuildParams& bp, int num_sms, cudaStream_t st) {
+  paper_rows_kernel<SNN_EXACT_F32W, false><<<num_sms * 8, kBuildWarps * 32, 0, st>>>(bp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_paper_fill(const BuildParams& bp, int precision, int num_sms,
+                              cudaStream_t st) {
+  if (precision == SNN_EXACT_F16W)
+    paper_rows_kernel<SNN_EXACT_F16W, true><<<num_sms * 8, kBuildWarps * 32, 0, st>>>(bp);
+  else
+    paper_rows_kernel<SNN_EXACT_F32W, true><<<num_sms * 8, kBuildWarps * 32, 0, st>>>(bp);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_build(const BuildParams& bp, int precision, int num_sms,
                          cudaStream_t st) {

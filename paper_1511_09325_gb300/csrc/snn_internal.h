@@ -47,6 +47,7 @@ constexpr uint32_t kTagConn = 1u;  // Philox counter word 2 of each stream
 constexpr uint32_t kTagExt = 2u;
 constexpr uint32_t kTagInit = 3u;
 constexpr uint32_t kTagSurr = 4u;  // normal draws of the differentiable form
+constexpr uint32_t kTagPConn = 5u; // candidate draws of the paper connectivity law
 constexpr int kMaxDelays = 32;   // d_max <= 32
 constexpr int kBendStride = 32;  // bytes of bucket ends per neuron
 constexpr int kSlotUnit = 8;     // buckets are padded to 8 synapse slots
@@ -69,6 +70,12 @@ struct HostTables {
   int32_t jx = 0;
   int nref = 0;
   int k_local = 0;
+  // paper connectivity law (SNN_CONN_PAPER)
+  int n_poff = 0;
+  int8_t poff_dx[kMaxOff] = {}, poff_dy[kMaxOff] = {};
+  unsigned long long poff_thr[kMaxOff] = {};  // candidate kept iff word < thr
+  unsigned long long plocal_thr = 0;
+  long long n_cand = 0;                        // candidates per neuron
 };
 
 int make_host_tables(const snn_neuron_params& np, const snn_synapse_params& sp,
@@ -118,6 +125,8 @@ struct StepParams {
   unsigned long long* colcnt;
   unsigned long long* ext_part;  // external-event partial sums, one per update block
   unsigned long long* spk_part;  // spike partial sums, one per update block
+  const uint32_t* deg;           // out-degree per neuron (paper law), else null
+  unsigned long long* syn_part;  // synaptic events of the spikes, one per update block
 };
 
 // A batch of nets advanced by one persistent launch (snn_batch_*).
@@ -142,6 +151,14 @@ struct BuildParams {
   const uint32_t* wtab;
   void* syn;
   uint8_t* bend;
+  // paper connectivity law
+  int n_poff;
+  long long n_cand;
+  unsigned long long poff_thr[kMaxOff];
+  unsigned long long plocal_thr;
+  int8_t poff_dx[kMaxOff], poff_dy[kMaxOff];
+  uint32_t* deg;          // [N] out-degree of each neuron
+  unsigned* max_units;    // largest row, in units of 8 slots
 };
 
 // What the differentiable form reads of a net (snn_api.cu fills it).
@@ -163,6 +180,11 @@ int validate_neuron_params(const snn_neuron_params* n, std::string* why);
 // Kernel launchers (snn_build.cu / snn_step.cu).
 cudaError_t launch_build(const BuildParams& bp, int precision, int num_sms,
                          cudaStream_t st);
+// Paper connectivity law: the count pass writes bend, deg and max_units; the
+// fill pass (same draws) writes the rows.
+cudaError_t launch_paper_count(const BuildParams& bp, int num_sms, cudaStream_t st);
+cudaError_t launch_paper_fill(const BuildParams& bp, int precision, int num_sms,
+                              cudaStream_t st);
 cudaError_t launch_init_state(const StepParams& p, cudaStream_t st);
 cudaError_t launch_update(const StepParams& p, int grid, cudaStream_t st);
 int update_grid(long long N, int num_sms);

@@ -123,6 +123,7 @@ struct UpdateSmem {
   long long cbase;               // compact list: position of the tile's first spike
   unsigned long long rbase;      // record position of the tile's first spike
   unsigned long long rc, spk;
+  unsigned long long syn;        // synaptic events of the block's spikes
   unsigned ksum[kUpdateThreads / 32];
 };
 
@@ -140,6 +141,7 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
   if (threadIdx.x == 0) {
     S.rc = P.rcnt[vb];
     S.spk = 0ull;
+    S.syn = 0ull;
   }
   unsigned ksum = 0u;
   const long long quads = (P.N + 3) / 4;
@@ -253,6 +255,8 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
         const unsigned off = (rank[e] & 0x80000000u) ? S.tpop[k][0] + r : r;
         const uint32_t id = (uint32_t)(i0 + e);
         list[P.ccnt != nullptr ? S.lbase[k] + off : S.cbase + S.tpos[k] + off] = id;
+        if (P.syn_part != nullptr)
+          atomicAdd(&S.syn, (unsigned long long)(P.deg != nullptr ? P.deg[id] : (uint32_t)P.K));
         const unsigned long long ri = rc + S.tpos[k] + off;
         if ((long long)ri < P.rec_region) region[ri] = ((unsigned long long)(unsigned)t << 32) | id;
       }
@@ -274,6 +278,7 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
     for (int w = 0; w < kUpdateThreads / 32; ++w) tot += S.ksum[w];
     P.ext_part[vb] += tot;
     P.spk_part[vb] += S.spk;
+    if (P.syn_part != nullptr) P.syn_part[vb] += S.syn;
     if ((long long)S.rc > P.rec_region) P.ctl->rec_overflow = 1u;
     P.rcnt[vb] = S.rc;
   }

@@ -151,12 +151,40 @@ int make_neuron_tables(const snn_neuron_params& np, HostTables* t, std::string* 
   return SNN_OK;
 }
 
+// Sec. 2's own law: offsets (dy-major, dx ascending, within 7x7) whose
+// probability a exp(-r^2 / (2 sigma^2)) reaches the cut-off, each with the
+// 32-bit threshold floor(P 2^32); the own column's threshold; the number of
+// candidates per neuron (the column's other neurons, then n_per_col per
+// offset).  Returns false when an offset beyond the 7x7 stencil would be kept.
+static bool paper_table(const snn_synapse_params& sp, int npc, HostTables* t) {
+  const double s2 = 2.0 * (double)sp.remote_sigma * (double)sp.remote_sigma;
+  int n = 0;
+  for (int dy = -3; dy <= 3; ++dy)
+    for (int dx = -3; dx <= 3; ++dx) {
+      if (dx == 0 && dy == 0) continue;
+      const double pr = (double)sp.remote_a * std::exp(-(double)(dx * dx + dy * dy) / s2);
+      if (pr < (double)sp.remote_cutoff) continue;
+      t->poff_dx[n] = (int8_t)dx;
+      t->poff_dy[n] = (int8_t)dy;
+      t->poff_thr[n] = (unsigned long long)std::floor(pr * 4294967296.0);
+      ++n;
+    }
+  t->n_poff = n;
+  t->plocal_thr = (unsigned long long)std::floor((double)sp.p_local * 4294967296.0);
+  t->n_cand = (long long)(npc - 1) + (long long)n * npc;
+  return (double)sp.remote_a * std::exp(-16.0 / s2) < (double)sp.remote_cutoff;
+}
+
 int make_host_tables(const snn_neuron_params& np, const snn_synapse_params& sp,
                      int precision, HostTables* t, std::string* err) {
   stencil_table(sp.stencil_radius, (double)sp.lambda_cols, t);
   int rc = make_neuron_tables(np, t, err);
   if (rc != SNN_OK) return rc;
   t->k_local = (int)std::rint((double)sp.frac_local * (double)sp.k_out);
+  if (sp.connectivity == SNN_CONN_PAPER && !paper_table(sp, np.n_per_col, t)) {
+    *err = "the paper law keeps offsets beyond the 7x7 stencil";
+    return SNN_EINVAL;
+  }
 
   // Weights: w = mu (1 + cv Q), clipped to the source population's sign,
   // then stored as float bits (F32W) or half magnitude bits (F16W).

@@ -21,7 +21,7 @@ PRECISIONS = {"f32w": SNN_EXACT_F32W, "f16w": SNN_EXACT_F16W}
 # every symbol the header declares
 EXPORTS = ("snn_build", "snn_step", "snn_read_spikes", "snn_pending_spikes",
            "snn_set_record_capacity", "snn_read_rates", "snn_stats", "snn_get_state",
-           "snn_read_synapses", "snn_info", "snn_step_profiled", "snn_update_noalloc",
+           "snn_read_synapses", "snn_row_lengths", "snn_info", "snn_step_profiled", "snn_update_noalloc",
            "snn_batch_build", "snn_batch_step", "snn_batch_net", "snn_batch_tune",
            "snn_batch_set_wait", "snn_batch_last_error", "snn_batch_destroy",
            "snn_grad_build", "snn_grad_run", "snn_grad_last_error", "snn_grad_destroy",
@@ -48,7 +48,10 @@ class SynapseParams(ctypes.Structure):
                 ("lambda_cols", ctypes.c_float), ("stencil_radius", ctypes.c_int32),
                 ("w_exc_mV", ctypes.c_float), ("w_inh_mV", ctypes.c_float),
                 ("w_cv", ctypes.c_float), ("d_min", ctypes.c_int32),
-                ("d_max", ctypes.c_int32), ("periodic", ctypes.c_int32)]
+                ("d_max", ctypes.c_int32), ("periodic", ctypes.c_int32),
+                ("connectivity", ctypes.c_int32), ("p_local", ctypes.c_float),
+                ("remote_a", ctypes.c_float), ("remote_sigma", ctypes.c_float),
+                ("remote_cutoff", ctypes.c_float)]
 
 
 _lib = None
@@ -74,6 +77,7 @@ def load(path=LIB_PATH):
     L.snn_stats.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double), P(i64)]
     L.snn_get_state.argtypes = [vp, vp, vp, vp]
     L.snn_read_synapses.argtypes = [vp, i64, i64, vp, vp, vp]
+    L.snn_row_lengths.argtypes = [vp, i64, i64, vp]
     L.snn_info.argtypes = [vp, vp, i32]
     L.snn_step_profiled.argtypes = [vp, i64, vp, vp]
     L.snn_update_noalloc.argtypes = [i32, i32, P(NeuronParams), ctypes.c_uint64, i64,
@@ -115,8 +119,13 @@ def neuron_struct(d):
     return NeuronParams(**{k: d[k] for k, _ in NeuronParams._fields_})
 
 
+SNN_CONN_FIXED, SNN_CONN_PAPER = 0, 1
+_SYN_DEFAULTS = dict(connectivity=SNN_CONN_FIXED, p_local=0.8, remote_a=0.05, remote_sigma=1.0,
+                     remote_cutoff=0.001)
+
+
 def synapse_struct(d):
-    return SynapseParams(**{k: d[k] for k, _ in SynapseParams._fields_})
+    return SynapseParams(**{k: d.get(k, _SYN_DEFAULTS.get(k)) for k, _ in SynapseParams._fields_})
 
 
 def snn_last_error(handle=None):
@@ -197,13 +206,26 @@ def snn_get_state(handle, n):
     return v, c, r
 
 
-def snn_read_synapses(handle, j0, n, k_out):
-    tgt = np.zeros(n * k_out, np.int64)
-    d = np.zeros(n * k_out, np.int32)
-    w = np.zeros(n * k_out, np.int32)
+def snn_row_lengths(handle, j0, n):
+    c = np.zeros(max(n, 1), np.int32)
+    _check(load().snn_row_lengths(handle, int(j0), int(n), _p(c)), handle)
+    return c[:n]
+
+
+def snn_read_synapses(handle, j0, n, k_out=None):
+    """Rows j0..j0+n-1: (target, delay, wfx) as [n, k_out] arrays when every
+    row has k_out synapses (pass k_out), else flat arrays in row order (see
+    snn_row_lengths)."""
+    total = int(snn_row_lengths(handle, j0, n).sum())
+    tgt = np.zeros(max(total, 1), np.int64)
+    d = np.zeros(max(total, 1), np.int32)
+    w = np.zeros(max(total, 1), np.int32)
     _check(load().snn_read_synapses(handle, int(j0), int(n), _p(tgt), _p(d), _p(w)), handle)
-    sh = (n, k_out)
-    return tgt.reshape(sh), d.reshape(sh), w.reshape(sh)
+    tgt, d, w = tgt[:total], d[:total], w[:total]
+    if k_out is not None and total == n * k_out:
+        sh = (n, k_out)
+        return tgt.reshape(sh), d.reshape(sh), w.reshape(sh)
+    return tgt, d, w
 
 
 def snn_info(handle):
@@ -440,6 +462,9 @@ class Net:
 
     def synapses(self, j0, n):
         return snn_read_synapses(self.handle, j0, n, self.k_out)
+
+    def row_lengths(self, j0, n):
+        return snn_row_lengths(self.handle, j0, n)
 
     def info(self):
         return snn_info(self.handle)

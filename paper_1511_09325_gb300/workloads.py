@@ -70,6 +70,11 @@ WORKLOADS = {
     # 96x96 columns, 11.43 M neurons, 14.17 G synapses (Table 1).
     "cols96x96_f16w": dict(grid_w=96, grid_h=96, seed=3, precision="f16w", steps=10000),
     "cols96x96_f32w": dict(grid_w=96, grid_h=96, seed=3, precision="f32w", steps=10000),
+    # Sec. 2's own connectivity law (variable out-degree, ~1307 synapses).
+    "cols2x2_paper_f32w": dict(grid_w=2, grid_h=2, seed=1, precision="f32w", steps=300,
+                               synapse=dict(connectivity=1)),
+    "cols24x24_paper_f32w": dict(grid_w=24, grid_h=24, seed=2, precision="f32w", steps=2000,
+                                 synapse=dict(connectivity=1)),
     # 4x4 columns: the size used for the single-column-neighbourhood tests.
     "cols4x4_f32w": dict(grid_w=4, grid_h=4, seed=5, precision="f32w", steps=500),
 }

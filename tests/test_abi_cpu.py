@@ -67,6 +67,19 @@ def test_invalid_synapse_params_rejected(lib, field, value):
     assert e.value.code == snn.SNN_EINVAL
 
 
+@pytest.mark.parametrize("over", [
+    dict(connectivity=2), dict(connectivity=1, p_local=1.5), dict(connectivity=1, remote_a=-0.1),
+    dict(connectivity=1, remote_sigma=0.0), dict(connectivity=1, remote_cutoff=0.0),
+    # sigma 2 keeps offsets at r = 4 (0.05 e^-2 = 0.0068 > 1e-3): wider than 7x7
+    dict(connectivity=1, remote_sigma=2.0),
+])
+def test_invalid_paper_law_rejected(lib, over):
+    s = W.synapse_params(**over)
+    with pytest.raises(snn.SnnError) as e:
+        snn.snn_build(2, 2, W.neuron_params(), s, 1, "f32w")
+    assert e.value.code == snn.SNN_EINVAL
+
+
 def test_invalid_grid_and_precision_rejected(lib):
     for gw, gh, prec in ((0, 2, 0), (2, -1, 0), (2, 2, 7)):
         with pytest.raises(snn.SnnError) as e:
