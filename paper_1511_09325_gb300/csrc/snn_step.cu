@@ -123,7 +123,7 @@ struct UpdateSmem {
   long long cbase;               // compact list: position of the tile's first spike
   unsigned long long rbase;      // record position of the tile's first spike
   unsigned long long rc, spk;
-  unsigned long long syn;        // synaptic events of the block's spikes
+  unsigned long long synw[kUpdateThreads / 32];  // synaptic events per warp
   unsigned ksum[kUpdateThreads / 32];
 };
 
@@ -141,9 +141,9 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
   if (threadIdx.x == 0) {
     S.rc = P.rcnt[vb];
     S.spk = 0ull;
-    S.syn = 0ull;
   }
   unsigned ksum = 0u;
+  unsigned long long syn = 0ull;  // out-degrees of this thread's spikes
   const long long quads = (P.N + 3) / 4;
   const long long tiles = (quads + kUpdateThreads - 1) / kUpdateThreads;
   uint32_t* list = P.ids + (long long)slot * P.N;
@@ -255,8 +255,7 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
         const unsigned off = (rank[e] & 0x80000000u) ? S.tpop[k][0] + r : r;
         const uint32_t id = (uint32_t)(i0 + e);
         list[P.ccnt != nullptr ? S.lbase[k] + off : S.cbase + S.tpos[k] + off] = id;
-        if (P.syn_part != nullptr)
-          atomicAdd(&S.syn, (unsigned long long)(P.deg != nullptr ? P.deg[id] : (uint32_t)P.K));
+        syn += P.deg != nullptr ? P.deg[id] : (uint32_t)P.K;
         const unsigned long long ri = rc + S.tpos[k] + off;
         if ((long long)ri < P.rec_region) region[ri] = ((unsigned long long)(unsigned)t << 32) | id;
       }
@@ -268,17 +267,26 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
     __syncthreads();
   }
 
-  // external events: per-block partial sum, no atomics
+  // external and synaptic events: per-block partial sums, no atomics
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ksum += __shfl_xor_sync(0xFFFFFFFFu, ksum, o);
-  if ((threadIdx.x & 31) == 0) S.ksum[threadIdx.x >> 5] = ksum;
+  for (int o = 16; o > 0; o >>= 1) {
+    ksum += __shfl_xor_sync(0xFFFFFFFFu, ksum, o);
+    syn += __shfl_xor_sync(0xFFFFFFFFu, syn, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    S.ksum[threadIdx.x >> 5] = ksum;
+    S.synw[threadIdx.x >> 5] = syn;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned long long tot = 0ull;
-    for (int w = 0; w < kUpdateThreads / 32; ++w) tot += S.ksum[w];
+    unsigned long long tot = 0ull, tsyn = 0ull;
+    for (int w = 0; w < kUpdateThreads / 32; ++w) {
+      tot += S.ksum[w];
+      tsyn += S.synw[w];
+    }
     P.ext_part[vb] += tot;
     P.spk_part[vb] += S.spk;
-    if (P.syn_part != nullptr) P.syn_part[vb] += S.syn;
+    if (P.syn_part != nullptr) P.syn_part[vb] += tsyn;
     if ((long long)S.rc > P.rec_region) P.ctl->rec_overflow = 1u;
     P.rcnt[vb] = S.rc;
   }
