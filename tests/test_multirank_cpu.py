@@ -1,10 +1,11 @@
-"""Multi-process paths on CPU ranks (gloo, world size 2).
+"""Multi-process paths on CPU ranks (gloo, world sizes 2, 4 and 9).
 
 1. The paper distributes the columns of the grid over MPI processes that
-   exchange spikes every step (Sec. 2).  Here two ranks each own one column,
-   integrate only their own neurons (the dense restatement of the step) and
-   all-gather the spike vector once per step; the union of their rasters must
-   equal the single-process oracle's raster bit for bit.
+   exchange spikes every step (Sec. 2).  Here each rank owns a tile of
+   columns, integrates only its own neurons (the dense restatement of the
+   step) and all-gathers the spike vector once per step (the minimum delay is
+   one step, so one exchange per step suffices); the union of the ranks'
+   rasters must equal the single-process oracle's raster bit for bit.
 2. bench.py's whole-job reduction over N replicas takes the slowest rank's
    time and the sum of the ranks' events.
 """
@@ -35,7 +36,7 @@ def _init(rank, world, port):
     return dist
 
 
-def _partitioned_worker(rank, world, port, steps, out_dir):
+def _partitioned_worker(rank, world, port, steps, out_dir, gw, gh):
     sys.path[:0] = [ROOT, HERE]
     import torch
 
@@ -46,9 +47,11 @@ def _partitioned_worker(rank, world, port, steps, out_dir):
     dist = _init(rank, world, port)
     n = W.neuron_params(n_per_col=100, n_exc=80, nu_ext_kHz=3.0)
     s = W.synapse_params(k_out=120, d_max=6)
-    p = oracle.make_params(2, 1, n, s, 23)
+    p = oracle.make_params(gw, gh, n, s, 23)
     net = DenseNet(oracle, p, "f32w")
-    rows = np.arange(rank * 100, (rank + 1) * 100)
+    ncol = gw * gh  # rank r owns columns [r ncol / world, (r + 1) ncol / world)
+    c0, c1 = rank * ncol // world, (rank + 1) * ncol // world
+    rows = np.arange(c0 * 100, c1 * 100)
 
     def exchange(local):
         mine = torch.from_numpy(local.astype(np.uint8))
@@ -63,20 +66,22 @@ def _partitioned_worker(rank, world, port, steps, out_dir):
     dist.destroy_process_group()
 
 
-def test_column_partition_with_spike_exchange_matches_oracle(tmp_path, orc):
+@pytest.mark.parametrize("world,gw,gh", [(2, 2, 1), (4, 2, 2), (9, 3, 3)])
+def test_column_partition_with_spike_exchange_matches_oracle(tmp_path, orc, world, gw, gh):
     from paper_1511_09325_gb300 import workloads as W
 
-    steps = 150
-    mp.spawn(_partitioned_worker, args=(2, _free_port(), steps, str(tmp_path)), nprocs=2, join=True)
-    got = np.concatenate([np.load(tmp_path / ("raster%d.npy" % r)) for r in range(2)])
+    steps = 120
+    mp.spawn(_partitioned_worker, args=(world, _free_port(), steps, str(tmp_path), gw, gh),
+             nprocs=world, join=True)
+    got = np.concatenate([np.load(tmp_path / ("raster%d.npy" % r)) for r in range(world)])
     n = W.neuron_params(n_per_col=100, n_exc=80, nu_ext_kHz=3.0)
     s = W.synapse_params(k_out=120, d_max=6)
-    o = orc.run(orc.make_params(2, 1, n, s, 23), "f32w", steps)
-    key = lambda a: np.sort(a[:, 0] * 1000 + a[:, 1])
+    o = orc.run(orc.make_params(gw, gh, n, s, 23), "f32w", steps)
+    key = lambda a: np.sort(a[:, 0] * 100000 + a[:, 1])
     want = np.stack([o["t"], o["i"]], 1).astype(np.int64)
     assert len(want) > 200
     assert np.array_equal(key(got), key(want))
-    v = np.concatenate([np.load(tmp_path / ("v%d.npy" % r)) for r in range(2)])
+    v = np.concatenate([np.load(tmp_path / ("v%d.npy" % r)) for r in range(world)])
     assert np.array_equal(v, o["v"])
 
 
