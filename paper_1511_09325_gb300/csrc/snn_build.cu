@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
     __syncwarp();
 
     const long long row = j * (long long)P.rowcap;
-    const int col = (int)(j / P.npc);
+    const int col = (int)((uint32_t)j / (uint32_t)P.npc);
     const int lj = (int)(j - (long long)col * P.npc);
     const uint32_t* wt = P.wtab + (lj < P.nexc ? 0 : 65536);
     // pass 2: regenerate and place every synapse
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) paper_rows_kernel(const Buil
 
   for (long long j = (long long)blockIdx.x * kBuildWarps + w; j < P.N; j += nwarps) {
     const uint32_t jj = (uint32_t)j;
-    const int col = (int)(j / P.npc);
+    const int col = (int)((uint32_t)j / (uint32_t)P.npc);
     const int lj = (int)(j - (long long)col * P.npc);
     const int cy = col / P.W, cx = col - cy * P.W;
     const uint32_t* wt = P.wtab + (lj < P.nexc ? 0 : 65536);
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) paper_rows_kernel(const Buil
           lq[q] = (int)c + ((int)c >= lj ? 1 : 0);
         } else {
           const long long r = c - (P.npc - 1);
-          const int m = (int)(r / P.npc);
+          const int m = (int)((uint32_t)r / (uint32_t)P.npc);
           thr = s_thr[m];
           mq[q] = m;
           lq[q] = (int)(r - (long long)m * P.npc);

@@ -81,6 +81,11 @@ struct GradParams {
   double* gacc;               // [6][N] parameter partials per neuron
 };
 
+// Ring position of step s >= 0 (steps are below 2^31: 32-bit remainder).
+__device__ __forceinline__ long long ring(long long s, int n) {
+  return (long long)((uint32_t)s % (uint32_t)n);
+}
+
 __device__ __forceinline__ float normal_draw(const GradParams& P, long long i, long long t) {
   const uint4 x = philox4x32_10(make_uint4((uint32_t)(i >> 2), (uint32_t)t, kTagSurr, 0u),
                                 P.seed_lo, P.seed_hi);
@@ -131,11 +136,11 @@ __global__ void __launch_bounds__(kThreads) grad_deliver_kernel(const GradParams
   int end_lane = 0x7FFFFFFF;
   if (lane < P.ndel) {
     const long long src = t - (P.dmin + lane);
-    s_lane = src >= 0 ? P.shist[(src % P.nslot) * P.N + j] : 0.f;
+    s_lane = src >= 0 ? P.shist[ring(src, P.nslot) * P.N + j] : 0.f;
     end_lane = (int)P.bend[j * kBendStride + lane] * kSlotUnit;
   }
   if (__ballot_sync(0xFFFFFFFFu, s_lane != 0.f) == 0u) return;
-  const bool exc = (int)(j % P.npc) < P.nexc;
+  const bool exc = (int)((uint32_t)j % (uint32_t)P.npc) < P.nexc;
   unsigned long long* acc = exc ? P.xe : P.xin;
   const int row_end = __shfl_sync(0xFFFFFFFFu, end_lane, P.ndel - 1);
   const uint2* row = P.syn + j * (long long)P.rowcap;
@@ -174,14 +179,14 @@ __global__ void __launch_bounds__(kThreads) grad_update_kernel(const GradParams 
     const float XI = __fmul_rn(__ll2float_rn((long long)P.xin[i]), kTwoM32);
     P.xe[i] = 0ull;
     P.xin[i] = 0ull;
-    exc = (int)(i % P.npc) < P.nexc;
+    exc = (int)((uint32_t)i % (uint32_t)P.npc) < P.nexc;
     const float xi = normal_draw(P, i, t);
     const float e = __fmul_rn(P.J, __fadd_rn(P.lam, __fmul_rn(P.sqlam, xi)));
     const float aE = exc ? P.a[0] : P.a[1];
     const float aI = exc ? P.a[2] : P.a[3];
     const float I = __fadd_rn(__fadd_rn(__fmul_rn(aE, XE), __fmul_rn(aI, XI)), e);
-    const float s1 = t >= 1 ? P.shist[((t - 1) % P.nslot) * P.N + i] : 0.f;
-    const float s2 = t >= 2 ? P.shist[((t - 2) % P.nslot) * P.N + i] : 0.f;
+    const float s1 = t >= 1 ? P.shist[ring(t - 1, P.nslot) * P.N + i] : 0.f;
+    const float s2 = t >= 2 ? P.shist[ring(t - 2, P.nslot) * P.N + i] : 0.f;
     const float V = P.V[i], c = P.C[i];
     float g, U, Vp, cp;
     if (P.hard) {
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) grad_update_kernel(const GradParams 
     const float pvc = exc ? P.pvc_e : P.pvc_i;
     P.V[i] = __fmaf_rn(cp, pvc, __fmul_rn(Vp, P.pvv));
     P.C[i] = __fmul_rn(cp, P.pcc);
-    P.shist[(t % P.nslot) * P.N + i] = s;
+    P.shist[ring(t, P.nslot) * P.N + i] = s;
     if (slot >= 0) {
       float* tp = P.tape + (long long)slot * kTape * P.N + i;
       const float vals[kTape] = {V, I, U, g, s, cp, XE, XI};
@@ -242,13 +247,13 @@ __global__ void __launch_bounds__(kThreads) grad_gather_kernel(const GradParams 
   const long long j = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (j >= P.N) return;
-  const bool exc = (int)(j % P.npc) < P.nexc;
+  const bool exc = (int)((uint32_t)j % (uint32_t)P.npc) < P.nexc;
   const float* ib = exc ? P.ibe : P.ibi;
   long long off_lane = -1;  // ring offset of bucket `lane`'s step, -1 beyond T
   int end_lane = 0x7FFFFFFF;
   if (lane < P.ndel) {
     const long long dst = tau + P.dmin + lane;
-    off_lane = dst < P.T ? (dst % P.nslot) * P.N : -1;
+    off_lane = dst < P.T ? ring(dst, P.nslot) * P.N : -1;
     end_lane = (int)P.bend[j * kBendStride + lane] * kSlotUnit;
   }
   const int row_end = __shfl_sync(0xFFFFFFFFu, end_lane, P.ndel - 1);
@@ -281,12 +286,12 @@ __global__ void __launch_bounds__(kThreads) grad_backward_kernel(const GradParam
                                                                 int slot) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P.N) return;
-  const bool exc = (int)(i % P.npc) < P.nexc;
+  const bool exc = (int)((uint32_t)i % (uint32_t)P.npc) < P.nexc;
   const float* tp = P.tape + (long long)slot * kTape * P.N + i;
   const float V = tp[0], I = tp[P.N], U = tp[2 * P.N], g = tp[3 * P.N], s = tp[4 * P.N];
   const float cp = tp[5 * P.N], XE = tp[6 * P.N], XI = tp[7 * P.N];
-  float sbar = (exc ? P.dlds_e : P.dlds_i) + P.sg[i] + P.gb[((tau + 1) % 3) * P.N + i] +
-               P.gb[((tau + 2) % 3) * P.N + i];
+  float sbar = (exc ? P.dlds_e : P.dlds_i) + P.sg[i] + P.gb[ring(tau + 1, 3) * P.N + i] +
+               P.gb[ring(tau + 2, 3) * P.N + i];
   const float vb1 = P.vbar[i], cb1 = P.cbar[i];
   const float pvc = exc ? P.pvc_e : P.pvc_i;
   // V(tau+1) = P_VV V' + P_VC c',  c(tau+1) = P_CC c'
@@ -310,11 +315,11 @@ __global__ void __launch_bounds__(kThreads) grad_backward_kernel(const GradParam
   const float ib = ubar * g;
   P.vbar[i] = ib;
   P.cbar[i] = cpbar;
-  P.gb[(tau % 3) * P.N + i] = g > 0.f ? -ubar * (V + I - P.vr) : 0.f;
+  P.gb[ring(tau, 3) * P.N + i] = g > 0.f ? -ubar * (V + I - P.vr) : 0.f;
   const float aE = exc ? P.a[0] : P.a[1];
   const float aI = exc ? P.a[2] : P.a[3];
-  P.ibe[(tau % P.nslot) * P.N + i] = aE * ib;
-  P.ibi[(tau % P.nslot) * P.N + i] = aI * ib;
+  P.ibe[ring(tau, P.nslot) * P.N + i] = aE * ib;
+  P.ibi[ring(tau, P.nslot) * P.N + i] = aI * ib;
   // I = a[E][p] X_E + a[I][p] X_I + J (lam + sqrt(lam) xi),  h = 1 ms
   ga[(exc ? 0 : 1) * P.N] += (double)ib * (double)XE;
   ga[(exc ? 2 : 3) * P.N] += (double)ib * (double)XI;

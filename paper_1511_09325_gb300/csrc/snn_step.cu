@@ -162,8 +162,9 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
   for (long long tile = vb; tile < tiles; tile += vgrid) {
     const long long first = tile * kTile;
     const long long last = (first + kTile < P.N ? first + kTile : P.N) - 1;
-    const int col0 = (int)(first / P.npc);
-    const int ncols = (int)(last / P.npc) - col0 + 1;
+    // neuron indices are below 2^31: 32-bit divisions are exact (and cheap)
+    const int col0 = (int)((uint32_t)first / (uint32_t)P.npc);
+    const int ncols = (int)((uint32_t)last / (uint32_t)P.npc) - col0 + 1;
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
       S.tpop[k][0] = 0u;
       S.tpop[k][1] = 0u;
@@ -188,8 +189,8 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
       const uint32_t xin[4] = {x.x, x.y, x.z, x.w};
       float vout[4], cout[4];
       uint32_t rout[4];
-      int col = (int)(i0 / P.npc);
-      int l = (int)(i0 - (long long)col * P.npc);
+      int col = (int)((uint32_t)i0 / (uint32_t)P.npc);
+      int l = (int)((uint32_t)i0 - (uint32_t)col * (uint32_t)P.npc);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int k = poisson_count(xin[e], S.guide, S.thr, P.n_pois_thr);
