@@ -45,16 +45,15 @@ struct snn_net {
   long long rec_cap = 0;     // requested total record capacity
   long long rec_region = 0;  // records per update block
   unsigned long long* rcnt = nullptr;
-  unsigned long long* stage = nullptr;   // drained records, contiguous
-  unsigned long long* rpre = nullptr;    // records kept before each region
-  unsigned long long* dhdr = nullptr;    // drain header (device)
+  unsigned long long* stage = nullptr;   // large drains on the device: ids then steps (u32)
+  unsigned long long* dhdr = nullptr;    // drain header (device, 4 words)
   unsigned long long* hhdr = nullptr;    // drain header (pinned, mapped)
   unsigned long long* hhdr_dev = nullptr;
-  unsigned long long* hmap = nullptr;    // drained records, small drains (pinned, mapped)
-  unsigned long long* hmap_dev = nullptr;
-  long long hmap_cap = 0;
-  unsigned long long* hstage = nullptr;  // drained records, large drains (pinned host)
-  long long hstage_cap = 0;
+  uint32_t* hmap = nullptr;              // small drains: ids then steps (pinned, mapped)
+  uint32_t* hmap_dev = nullptr;
+  long long hmap_cap = 0;                // records
+  uint32_t* hstage = nullptr;            // large drains: ids then steps (pinned host)
+  long long hstage_cap = 0;              // records
   unsigned long long* colcnt = nullptr;
   unsigned long long* ext_part = nullptr;
   unsigned long long* spk_part = nullptr;
@@ -146,7 +145,7 @@ void release(snn_net* net) {
   if (net->hmap) cudaFreeHost(net->hmap);
   if (net->hstage) cudaFreeHost(net->hstage);
   void* ptrs[] = {net->syn, net->bend, net->V, net->C, net->R, net->acc,
-                  net->ids, net->cnt, net->ccnt, net->deg, net->syn_part, net->isum, net->gsum, net->ctl, net->rec, net->rcnt, net->stage, net->rpre, net->dhdr, net->colcnt,
+                  net->ids, net->cnt, net->ccnt, net->deg, net->syn_part, net->isum, net->gsum, net->ctl, net->rec, net->rcnt, net->stage, net->dhdr, net->colcnt,
                   net->ext_part, net->spk_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -365,9 +364,8 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if ((rc = dalloc(net, &net->rec, (size_t)net->rec_region * net->update_grid * 8))) return rc;
   if ((rc = dalloc(net, &net->rcnt, (size_t)net->update_grid * 8))) return rc;
   if ((rc = dalloc(net, &net->stage, (size_t)net->rec_region * net->update_grid * 8))) return rc;
-  if ((rc = dalloc(net, &net->dhdr, 16))) return rc;
-  if ((rc = dalloc(net, &net->rpre, (size_t)net->update_grid * 8))) return rc;
-  SNN_CUDA(net, cudaHostAlloc(&net->hhdr, 16, cudaHostAllocMapped));
+  if ((rc = dalloc(net, &net->dhdr, 32))) return rc;
+  SNN_CUDA(net, cudaHostAlloc(&net->hhdr, 32, cudaHostAllocMapped));
   SNN_CUDA(net, cudaHostGetDevicePointer(&net->hhdr_dev, net->hhdr, 0));
   net->hmap_cap = std::min<long long>(net->rec_region * net->update_grid, kMappedRecords);
   SNN_CUDA(net, cudaHostAlloc(&net->hmap, (size_t)net->hmap_cap * 8, cudaHostAllocMapped));
@@ -605,17 +603,21 @@ int snn_read_spikes(snn_net* net, int32_t* steps, int32_t* ids, int64_t cap, int
   if (!net || !n_out || cap < 0 || (cap > 0 && (!steps || !ids)))
     return fail(net, SNN_EINVAL, "bad argument");
   *n_out = 0;
-  // compact the regions on the device and reset them; a drain of at most
-  // hmap_cap records lands in mapped host memory directly, a larger one is
-  // copied from the device stage afterwards
-  SNN_CUDA(net, launch_drain_records(net->sp, net->update_grid, net->rpre, net->stage,
-                                     net->dhdr, net->hhdr_dev, net->hmap_dev, net->hmap_cap,
-                                     net->stream));
+  // compact the regions on the device into id and step arrays and reset
+  // them; a drain of at most hmap_cap records lands in mapped host memory
+  // directly, a larger one is copied from the device stage afterwards
+  const long long stage_cap = net->rec_region * net->update_grid;
+  uint32_t* stage_ids = reinterpret_cast<uint32_t*>(net->stage);
+  SNN_CUDA(net, launch_drain_records(net->sp, net->update_grid, stage_ids, stage_ids + stage_cap,
+                                     net->dhdr, net->hhdr_dev, net->hmap_dev,
+                                     net->hmap_dev + net->hmap_cap, net->hmap_cap, net->stream));
   SNN_CUDA(net, cudaStreamSynchronize(net->stream));
   const long long kept = (long long)net->hhdr[0];
   bool lost = net->hhdr[1] != 0ull || kept > cap;
+  const uint32_t tmin = (uint32_t)net->hhdr[2], tmax = (uint32_t)net->hhdr[3];
   const long long n = kept < cap ? kept : cap;
-  const unsigned long long* h = net->hmap;
+  const uint32_t* hid = net->hmap;
+  const uint32_t* hst = net->hmap + net->hmap_cap;
   if (n > 0 && kept > net->hmap_cap) {
     if (n > net->hstage_cap) {
       if (net->hstage) cudaFreeHost(net->hstage);
@@ -625,34 +627,29 @@ int snn_read_spikes(snn_net* net, int32_t* steps, int32_t* ids, int64_t cap, int
       SNN_CUDA(net, cudaMallocHost(&net->hstage, (size_t)want * 8));
       net->hstage_cap = want;
     }
-    SNN_CUDA(net, cudaMemcpyAsync(net->hstage, net->stage, (size_t)n * 8, cudaMemcpyDeviceToHost,
+    SNN_CUDA(net, cudaMemcpyAsync(net->hstage, stage_ids, (size_t)n * 4, cudaMemcpyDeviceToHost,
                                   net->stream));
+    SNN_CUDA(net, cudaMemcpyAsync(net->hstage + net->hstage_cap, stage_ids + stage_cap,
+                                  (size_t)n * 4, cudaMemcpyDeviceToHost, net->stream));
     SNN_CUDA(net, cudaStreamSynchronize(net->stream));
-    h = net->hstage;
+    hid = net->hstage;
+    hst = net->hstage + net->hstage_cap;
   }
   if (n > 0) {
-    // each region is in step order: a counting sort by step puts the window
-    // in step order (within a step the order stays unspecified)
-    uint32_t tmin = 0xFFFFFFFFu, tmax = 0u;
-    for (long long k = 0; k < n; ++k) {
-      const uint32_t t = (uint32_t)(h[k] >> 32);
-      tmin = t < tmin ? t : tmin;
-      tmax = t > tmax ? t : tmax;
-    }
     if (tmin == tmax) {
-      for (long long k = 0; k < n; ++k) {
-        steps[k] = (int32_t)tmin;
-        ids[k] = (int32_t)(h[k] & 0xFFFFFFFFull);
-      }
+      // one step (the usual read after every step): the ids as they are
+      std::memcpy(ids, hid, (size_t)n * 4);
+      std::fill(steps, steps + n, (int32_t)tmin);
     } else {
+      // each region is in step order: a counting sort by step puts the
+      // window in step order (within a step the order stays unspecified)
       std::vector<long long> pos((size_t)(tmax - tmin) + 2, 0);
-      for (long long k = 0; k < n; ++k) ++pos[(size_t)((uint32_t)(h[k] >> 32) - tmin) + 1];
+      for (long long k = 0; k < n; ++k) ++pos[(size_t)(hst[k] - tmin) + 1];
       for (size_t i = 1; i < pos.size(); ++i) pos[i] += pos[i - 1];
       for (long long k = 0; k < n; ++k) {
-        const uint32_t t = (uint32_t)(h[k] >> 32);
-        const long long o = pos[t - tmin]++;
-        steps[o] = (int32_t)t;
-        ids[o] = (int32_t)(h[k] & 0xFFFFFFFFull);
+        const long long o = pos[hst[k] - tmin]++;
+        steps[o] = (int32_t)hst[k];
+        ids[o] = (int32_t)hid[k];
       }
     }
     *n_out = n;

@@ -88,7 +88,7 @@ const std::vector<double>& quantile_table();
 // Device control block.
 struct Ctl {
   long long t;                  // step index of the next update
-  unsigned int unused;
+  unsigned int drained;         // blocks done with the current record drain
   unsigned int done;            // delivery blocks finished this step
   unsigned int rec_overflow;    // set when a record did not fit its region
   unsigned int pad;
@@ -190,15 +190,16 @@ cudaError_t launch_update(const StepParams& p, int grid, cudaStream_t st);
 int update_grid(long long N, int num_sms);
 cudaError_t launch_deliver(const StepParams& p, int precision, int grid, cudaStream_t st);
 int deliver_grid(int precision, int num_sms, int npc, bool agg);
-// Compact the per-block record regions and reset them; header[0] = records
-// kept, header[1] = 1 if records were dropped (written to header and to the
-// mapped host header map_hdr).  The records go to the mapped host buffer map
-// when they number at most map_cap, else to the device buffer stage.
+// Compact the per-block record regions into id and step arrays and reset
+// them; header = {records kept, 1 if records were dropped, first step, last
+// step}, written to header and to the mapped host header map_hdr.  The arrays
+// go to the mapped host buffers when they hold at most map_cap records, else
+// to the device stage.
 constexpr long long kMappedRecords = 1LL << 18;  // mapped host records per net
-cudaError_t launch_drain_records(const StepParams& p, int nreg, unsigned long long* pre,
-                                 unsigned long long* stage, unsigned long long* header,
-                                 unsigned long long* map_hdr, unsigned long long* map,
-                                 long long map_cap, cudaStream_t st);
+cudaError_t launch_drain_records(const StepParams& p, int nreg, uint32_t* stage_ids,
+                                 uint32_t* stage_steps, unsigned long long* header,
+                                 unsigned long long* map_hdr, uint32_t* map_ids,
+                                 uint32_t* map_steps, long long map_cap, cudaStream_t st);
 size_t batch_smem(int max_npc);
 int batch_grid(int precision, int infl, int num_sms, int max_npc);
 cudaError_t launch_batch(const BatchParams& b, int precision, int infl, int grid, int max_npc,

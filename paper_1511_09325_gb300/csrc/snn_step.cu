@@ -775,77 +775,101 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchPara
     for (int k = threadIdx.x; k < n; k += blockDim.x) B.nets[k].ctl->t = B.t0 + B.n_steps;
 }
 
-// Spike-record drain, first kernel (one block): pre[b] = records kept in the
-// regions before b; header[0] = records kept, header[1] = 1 if any were
-// dropped (also written to the mapped host header map_hdr); clears the
-// overflow flag.
-__global__ void __launch_bounds__(1024) scan_records_kernel(const unsigned long long* rcnt,
-                                                            int nreg, long long region, Ctl* ctl,
-                                                            unsigned long long* pre,
-                                                            unsigned long long* header,
-                                                            unsigned long long* map_hdr) {
-  __shared__ unsigned long long s_w[32];
-  __shared__ unsigned s_l[32];
-  const int per = (nreg + blockDim.x - 1) / blockDim.x;
-  const int r0 = threadIdx.x * per;
-  unsigned long long mine = 0ull;
-  unsigned lost = 0u;
-  for (int r = r0; r < r0 + per && r < nreg; ++r) {
-    const unsigned long long v = rcnt[r];
-    mine += (long long)v < region ? v : (unsigned long long)region;
-    lost |= (long long)v > region ? 1u : 0u;
-  }
+// Spike-record drain, one kernel.  Block b copies the records kept in region
+// b (rcnt[b], at most `region`; records are step << 32 | id) as separate id
+// and step arrays, starting at the number of records kept in the regions
+// before b, to the mapped host buffers when all kept records fit them
+// (map_cap) and to the device stage otherwise.  Block 0 writes the header
+// {records kept, 1 if any were dropped, first step, last step} to device and
+// mapped host memory (each region is in step order, so its first and last
+// records bound its steps).  The last block to finish resets the region
+// counters and the overflow flag.
+__global__ void __launch_bounds__(256) drain_records_kernel(
+    unsigned long long* rcnt, int nreg, long long region, const unsigned long long* rec,
+    Ctl* ctl, unsigned long long* header, unsigned long long* map_hdr, uint32_t* stage_ids,
+    uint32_t* stage_steps, uint32_t* map_ids, uint32_t* map_steps, long long map_cap) {
+  __shared__ unsigned long long s_pre[8], s_tot[8];
+  __shared__ unsigned s_tmin[8], s_tmax[8], s_lost[8];
+  __shared__ bool s_last;
+  const int b = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned long long incl = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += v;
+  unsigned long long pre = 0ull, tot = 0ull;
+  unsigned tmin = 0xFFFFFFFFu, tmax = 0u, lost = 0u;
+  for (int r = threadIdx.x; r < nreg; r += blockDim.x) {
+    const unsigned long long v = rcnt[r];
+    const unsigned long long kept = (long long)v < region ? v : (unsigned long long)region;
+    lost |= (long long)v > region ? 1u : 0u;
+    tot += kept;
+    if (r < b) pre += kept;
+    if (b == 0 && kept > 0ull) {
+      const unsigned first = (unsigned)(rec[(long long)r * region] >> 32);
+      const unsigned lastt = (unsigned)(rec[(long long)r * region + (long long)kept - 1] >> 32);
+      tmin = min(tmin, first);
+      tmax = max(tmax, lastt);
+    }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) lost |= __shfl_xor_sync(0xFFFFFFFFu, lost, o);
-  if (lane == 31) {
-    s_w[w] = incl;
-    s_l[w] = lost;
+  for (int o = 16; o > 0; o >>= 1) {
+    pre += __shfl_xor_sync(0xFFFFFFFFu, pre, o);
+    tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
+    tmin = min(tmin, __shfl_xor_sync(0xFFFFFFFFu, tmin, o));
+    tmax = max(tmax, __shfl_xor_sync(0xFFFFFFFFu, tmax, o));
+    lost |= __shfl_xor_sync(0xFFFFFFFFu, lost, o);
+  }
+  if (lane == 0) {
+    s_pre[w] = pre;
+    s_tot[w] = tot;
+    s_tmin[w] = tmin;
+    s_tmax[w] = tmax;
+    s_lost[w] = lost;
   }
   __syncthreads();
-  unsigned long long before = 0ull;
-  unsigned any = 0u;
+  pre = 0ull;
+  tot = 0ull;
+  tmin = 0xFFFFFFFFu;
+  tmax = 0u;
+  lost = 0u;
   for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-    if (k < w) before += s_w[k];
-    any |= s_l[k];
+    pre += s_pre[k];
+    tot += s_tot[k];
+    tmin = min(tmin, s_tmin[k]);
+    tmax = max(tmax, s_tmax[k]);
+    lost |= s_lost[k];
   }
-  unsigned long long run = before + incl - mine;
-  for (int r = r0; r < r0 + per && r < nreg; ++r) {
-    pre[r] = run;
-    const unsigned long long v = rcnt[r];
-    run += (long long)v < region ? v : (unsigned long long)region;
+  if (b == 0 && threadIdx.x == 0) {
+    const unsigned long long h[4] = {tot, (lost || ctl->rec_overflow) ? 1ull : 0ull,
+                                     (unsigned long long)tmin, (unsigned long long)tmax};
+    for (int k = 0; k < 4; ++k) {
+      header[k] = h[k];
+      map_hdr[k] = h[k];
+    }
   }
-  if (threadIdx.x == blockDim.x - 1) {
-    const unsigned long long lost = (any || ctl->rec_overflow) ? 1ull : 0ull;
-    header[0] = before + incl;
-    header[1] = lost;
-    map_hdr[0] = before + incl;
-    map_hdr[1] = lost;
-    ctl->rec_overflow = 0u;
-  }
-}
-
-// Spike-record drain, second kernel: block b copies the records kept in
-// region b to position pre[b] of the mapped host buffer map (when all kept
-// records fit in it) or of stage, and empties the region.
-__global__ void copy_records_kernel(unsigned long long* rcnt, long long region,
-                                    const unsigned long long* rec, const unsigned long long* pre,
-                                    const unsigned long long* header, unsigned long long* stage,
-                                    unsigned long long* map, long long map_cap) {
-  const int b = blockIdx.x;
+  const bool to_map = (long long)tot <= map_cap;
+  uint32_t* ids = (to_map ? map_ids : stage_ids) + pre;
+  uint32_t* steps = (to_map ? map_steps : stage_steps) + pre;
   const unsigned long long v = rcnt[b];
   const long long kept = (long long)v < region ? (long long)v : region;
   const unsigned long long* src = rec + (long long)b * region;
-  unsigned long long* dst = ((long long)header[0] <= map_cap ? map : stage) + pre[b];
-  for (long long k = threadIdx.x; k < kept; k += blockDim.x) dst[k] = src[k];
+  for (long long k = threadIdx.x; k < kept; k += blockDim.x) {
+    const unsigned long long r = src[k];
+    ids[k] = (uint32_t)r;
+    steps[k] = (uint32_t)(r >> 32);
+  }
+  // the counters are read by every block: the last one to finish resets them
   __syncthreads();
-  if (threadIdx.x == 0) rcnt[b] = 0ull;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ctl->drained, 1u) == (unsigned)nreg - 1u;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (int r = threadIdx.x; r < nreg; r += blockDim.x) rcnt[r] = 0ull;
+    if (threadIdx.x == 0) {
+      ctl->rec_overflow = 0u;
+      ctl->drained = 0u;
+    }
+  }
 }
 
 // Sum of the per-block spike counts (measurement helper).
@@ -905,16 +929,13 @@ cudaError_t launch_deliver(const StepParams& p, int precision, int grid, cudaStr
   return cudaGetLastError();
 }
 
-cudaError_t launch_drain_records(const StepParams& p, int nreg, unsigned long long* pre,
-                                 unsigned long long* stage, unsigned long long* header,
-                                 unsigned long long* map_hdr, unsigned long long* map,
-                                 long long map_cap, cudaStream_t st) {
-  scan_records_kernel<<<1, 1024, 0, st>>>(p.rcnt, nreg, p.rec_region, p.ctl, pre, header,
-                                          map_hdr);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  copy_records_kernel<<<nreg, 256, 0, st>>>(p.rcnt, p.rec_region, p.rec, pre, header, stage, map,
-                                            map_cap);
+cudaError_t launch_drain_records(const StepParams& p, int nreg, uint32_t* stage_ids,
+                                 uint32_t* stage_steps, unsigned long long* header,
+                                 unsigned long long* map_hdr, uint32_t* map_ids,
+                                 uint32_t* map_steps, long long map_cap, cudaStream_t st) {
+  drain_records_kernel<<<nreg, 256, 0, st>>>(p.rcnt, nreg, p.rec_region, p.rec, p.ctl, header,
+                                             map_hdr, stage_ids, stage_steps, map_ids, map_steps,
+                                             map_cap);
   return cudaGetLastError();
 }
 
