@@ -313,6 +313,10 @@ constexpr int kWindows = 4;        // shared-memory windows (columns) per delive
 constexpr int kBatchItems = 16;    // items per warp batch (at most 32)
 // (column, bucket) entries per table piece, at most: 4 per thread
 constexpr int kTabEntries = 4 * (kDeliverThreads > kBatchThreads ? kDeliverThreads : kBatchThreads);
+// A piece spans at most kPieceCols columns; for F16W each has 64 entries
+// (one per stencil code) in the neighbour table.
+constexpr int kPieceCols = 32;
+constexpr int kNbEntries = 64 * kPieceCols;
 
 // Per-item info travelling with a chunk: the spiker's column cx | cy << 14
 // and whether it is inhibitory (bit 28).
@@ -328,18 +332,17 @@ __device__ __forceinline__ uint32_t pack_info(int cx, int cy, bool inh) {
 template <int PREC>
 __device__ __forceinline__ void deliver_record(uint32_t code, uint32_t wbits, uint32_t info,
                                                uint32_t win_s, uint32_t wbase, uint32_t wlen,
-                                               uint64_t pol, const StepParams& P) {
+                                               uint64_t pol, const uint32_t* nb,
+                                               const StepParams& P) {
   const bool valid = code != kPad;
   uint32_t target;
   int32_t wfx;
   if (PREC == SNN_EXACT_F16W) {
     const float wscale = (info >> 28) & 1u ? -65536.0f : 65536.0f;
     wfx = __float2int_rn(__fmul_rn(__half2float(__ushort_as_half((unsigned short)wbits)), wscale));
+    // first neuron of the target column, from the piece's neighbour table
     const uint32_t off = (code >> 11) & 63u;
-    const int cx = (int)(info & 0x3FFFu), cy = (int)((info >> 14) & 0x3FFFu);
-    const int ty = wrap_near(cy + (int)(off >> 3) - 3, P.H);
-    const int tx = wrap_near(cx + (int)(off & 7u) - 3, P.W);
-    target = ((uint32_t)ty * (uint32_t)P.W + (uint32_t)tx) * (uint32_t)P.npc + (code & 0x7FFu);
+    target = nb[(info & 0x3Fu) * 64u + (valid ? off : 0u)] + (code & 0x7FFu);
   } else {
     wfx = (int32_t)wbits;
     target = code;
@@ -394,7 +397,7 @@ template <int PREC, int INFL>
 __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item, unsigned hi,
                                               const DeliverSmem& S, int n_entries, int pc,
                                               uint32_t win_s, uint32_t wbase, uint32_t wlen,
-                                              uint64_t pol) {
+                                              uint64_t pol, const uint32_t* nb) {
   const int lane = threadIdx.x & 31;
   int len = 0;
   unsigned long long base = 0ull;
@@ -417,9 +420,13 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
     const int end = (int)be[b] * kSlotUnit;
     len = end - beg;
     base = (unsigned long long)j * (unsigned long long)P.rowcap + (unsigned long long)beg;
-    const int cy = c / P.W;
     const bool inh = (int)(j - (uint32_t)c * (uint32_t)P.npc) >= P.nexc;
-    info = pack_info(c - cy * P.W, cy, inh);
+    if (PREC == SNN_EXACT_F16W) {
+      info = (uint32_t)k | ((inh ? 1u : 0u) << 28);  // column within the piece
+    } else {
+      const int cy = c / P.W;
+      info = pack_info(c - cy * P.W, cy, inh);
+    }
   }
   // compact the non-empty items to lanes 0..nit-1
   const unsigned cm = __ballot_sync(0xFFFFFFFFu, len > 0);
@@ -497,7 +504,7 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
 #pragma unroll
       for (int qd = 0; qd < 4; ++qd)
         deliver_record<PREC>(in[u] ? code[u][qd] : kPad, wbits[u][qd], inf[u], win_s, wbase, wlen,
-                             pol, P);
+                             pol, nb, P);
     }
   }
 }
@@ -513,7 +520,7 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
 // once per piece.
 template <int PREC, int INFL>
 __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, int vb, int vgrid,
-                                             DeliverSmem& S, int32_t* win_base) {
+                                             DeliverSmem& S, int32_t* win_base, uint32_t* nb) {
   __syncthreads();  // the shared memory may still be read by a previous body
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -590,8 +597,8 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
 
   const uint64_t pol = evict_last_policy();
   const uint32_t win_s = (uint32_t)__cvta_generic_to_shared(win_base);
-  // a piece tabulates at most 4 entries per thread
-  const int cols_per_piece = min(kTabEntries, 4 * (int)blockDim.x) / P.ndel;
+  // a piece tabulates at most 4 entries per thread and kPieceCols columns
+  const int cols_per_piece = min(min(kTabEntries, 4 * (int)blockDim.x) / P.ndel, kPieceCols);
   unsigned long long pbase = S.p0;  // items before the piece's first column
   for (int pc = c0; pc <= c1; pc += cols_per_piece) {
     const int ncp = min(cols_per_piece, c1 - pc + 1);
@@ -623,6 +630,17 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
     __syncthreads();
     const unsigned a = lo > pbase ? (unsigned)(lo - pbase) : 0u;
     const unsigned b = hi > pbase ? (unsigned)min(hi - pbase, ptotal) : 0u;
+    if (PREC == SNN_EXACT_F16W) {
+      // first neuron of the column at each stencil offset of each column of
+      // the piece (periodic), for the records' column-relative targets
+      for (int m = threadIdx.x; m < ncp * 64; m += blockDim.x) {
+        const int c = pc + (m >> 6), off = m & 63;
+        const int cy = c / P.W, cx = c - cy * P.W;
+        const int ty = wrap(cy + (off >> 3) - 3, P.H), tx = wrap(cx + (off & 7) - 3, P.W);
+        nb[m] = ((uint32_t)ty * (uint32_t)P.W + (uint32_t)tx) * (uint32_t)P.npc;
+      }
+      __syncthreads();
+    }
     // windows: the piece's first columns, for synapses from any of its items
     const uint32_t wbase = (uint32_t)pc * (uint32_t)P.npc;
     const uint32_t wlen = P.agg ? (uint32_t)min(kWindows, ncp) * (uint32_t)P.npc : 0u;
@@ -633,7 +651,7 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
       if (a + k0 >= b) break;
       const unsigned end = min(b, a + k0 + (unsigned)kBatchItems);
       deliver_batch<PREC, INFL>(P, lane < kBatchItems ? a + k0 + lane : end, end, S, n_entries, pc,
-                                win_s, wbase, wlen, pol);
+                                win_s, wbase, wlen, pol, nb);
     }
     __syncthreads();
     // flush the windows with coalesced reductions, leaving them zeroed
@@ -654,8 +672,9 @@ template <int PREC>
 __global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepParams P) {
   extern __shared__ int32_t s_win[];  // [kWindows][n_per_col] when P.agg
   __shared__ DeliverSmem S;
+  __shared__ uint32_t s_nb[PREC == SNN_EXACT_F16W ? kNbEntries : 1];
   const long long t = P.ctl->t;
-  deliver_body<PREC, kInflight>(P, t, (int)blockIdx.x, (int)gridDim.x, S, s_win);
+  deliver_body<PREC, kInflight>(P, t, (int)blockIdx.x, (int)gridDim.x, S, s_win, s_nb);
 
   // the last block to finish closes the step
   __syncthreads();
@@ -738,6 +757,7 @@ template <int PREC, int INFL>
 __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchParams B) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ StepParams s_p;  // the current virtual block's net
+  __shared__ uint32_t s_nb[PREC == SNN_EXACT_F16W ? kNbEntries : 1];
   __shared__ int s_uf[kMaxBatch + 1], s_df[kMaxBatch + 1];
   __shared__ unsigned s_ok;
   UpdateSmem& SU = *reinterpret_cast<UpdateSmem*>(s_dyn);
@@ -767,7 +787,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchPara
       for (int w = threadIdx.x; w < (int)(sizeof(StepParams) / 4); w += blockDim.x)
         reinterpret_cast<uint32_t*>(&s_p)[w] = reinterpret_cast<const uint32_t*>(B.nets + k)[w];
       __syncthreads();
-      deliver_body<PREC, INFL>(s_p, t, g - s_df[k], s_df[k + 1] - s_df[k], SD, win);
+      deliver_body<PREC, INFL>(s_p, t, g - s_df[k], s_df[k + 1] - s_df[k], SD, win, s_nb);
     }
     if (!grid_barrier(B, &s_ok)) return;
   }
