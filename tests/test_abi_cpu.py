@@ -95,3 +95,17 @@ def test_calls_on_null_net_fail_cleanly(lib):
     assert lib.snn_step(None, 1) == snn.SNN_EINVAL
     assert lib.snn_stats(None, None, None, None) == snn.SNN_EINVAL
     assert lib.snn_last_error(None) is not None
+    assert lib.snn_row_lengths(None, 0, 1, None) == snn.SNN_EINVAL
+
+
+def test_gradient_entry_points_refuse_null_arguments(lib):
+    import ctypes
+
+    out = ctypes.c_void_p()
+    assert lib.snn_grad_build(None, 10, 5, 1, 5.0, None, ctypes.byref(out)) == snn.SNN_EINVAL
+    assert out.value is None
+    assert lib.snn_grad_build(None, 10, 5, 1, 5.0, None, None) == snn.SNN_EINVAL
+    loss = ctypes.c_double()
+    assert lib.snn_grad_run(None, None, ctypes.byref(loss), None, None) == snn.SNN_EINVAL
+    assert lib.snn_grad_last_error(None) == b""
+    lib.snn_grad_destroy(None)

@@ -78,6 +78,24 @@ def test_step_limit_is_the_spiking_model(grid, seed):
         assert np.max(np.abs(st["V_end"] - o["v"])) < 1e-9
 
 
+def test_normal_draws_are_standard_normal_and_keyed_as_stated(orc):
+    """xi_i(t) = Q[word >> 16], word = word i mod 4 of Philox(seed; i/4, t, 4):
+    the wiring against the oracle's own generator and table, and the draws
+    against N(0, 1) (moments and a Kolmogorov-Smirnov test)."""
+    from scipy import stats
+
+    p = orc.make_params(1, 1, W.neuron_params(), W.synapse_params(), 77)
+    xi = orc.surr_xi(p, 0, 1240, 0, 40)
+    q = orc.tables(p)["q"]
+    key = [77, 0]
+    for i, t in ((0, 0), (5, 3), (1239, 39), (402, 17)):
+        w = orc.philox([i >> 2, t, 4, 0], key)[i & 3]
+        assert xi[t, i] == q[int(w) >> 16]
+    x = xi.ravel()
+    assert abs(x.mean()) < 4 / np.sqrt(x.size) and abs(x.var() - 1) < 0.03
+    assert stats.kstest(x, "norm").pvalue > 1e-4
+
+
 def test_fp32_forward_has_the_fp64_spikes(net1):
     """Hard spikes, 100 steps: the exact-FP32 recursion fires exactly where the
     FP64 one does, and its gradient agrees to 1e-3."""
