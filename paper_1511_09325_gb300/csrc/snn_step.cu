@@ -37,7 +37,8 @@ namespace {
 constexpr int kUpdateThreads = 256;
 constexpr int kDeliverThreads = 256;
 constexpr int kBatchThreads = kUpdateThreads;  // the batch kernel runs both bodies
-constexpr int kInflight = 4;  // 16-byte synapse chunks in flight per lane
+constexpr int kInflight = 4;     // 16-byte synapse chunks in flight per lane (F32W: 2 loads each)
+constexpr int kInflightF16 = 4;  // the same for F16W (one load each)
 constexpr int kTile = kUpdateThreads * 4;    // neurons per update tile
 constexpr int kTileCols = kTile / 2 + 2;     // columns a tile can touch (npc >= 2)
 
@@ -451,19 +452,17 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
   const unsigned le_mask = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
 
   for (int f0 = 0; f0 < T; f0 += 128 * INFL) {
-    uint32_t code[INFL][4], wbits[INFL][4];
+    // the chunks' raw words: 4 per lane for F16W, 8 for F32W; padding where
+    // a lane has no chunk
+    constexpr int kWords = PREC == SNN_EXACT_F16W ? 4 : 8;
+    uint32_t raw[INFL][kWords];
     uint32_t inf[INFL];
-    bool in[INFL];
 #pragma unroll
     for (int u = 0; u < INFL; ++u) {
       const int fu = f0 + u * 128;
-      in[u] = false;
       inf[u] = 0u;
 #pragma unroll
-      for (int qd = 0; qd < 4; ++qd) {
-        code[u][qd] = kPad;
-        wbits[u][qd] = 0u;
-      }
+      for (int q = 0; q < kWords; ++q) raw[u][q] = kPad;
       if (fu < T) {
         // item of the chunk at flat slot fu + 4 * lane: the item holding fu,
         // plus the items that start between fu and the lane's chunk
@@ -476,25 +475,20 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
         const unsigned bh = __shfl_sync(0xFFFFFFFFu, bhi, e);
         inf[u] = __shfl_sync(0xFFFFFFFFu, infc, e);
         const int f = fu + 4 * lane;
-        in[u] = f < T;
-        if (in[u]) {
+        if (f < T) {
           const long long slot = (long long)(((unsigned long long)bh << 32) | bl) + f;
           if (PREC == SNN_EXACT_F16W) {
             const uint4 r = __ldcs(reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(P.syn) + slot));
-            const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-            for (int qd = 0; qd < 4; ++qd) {
-              code[u][qd] = rr[qd] == kPad ? kPad : (rr[qd] & 0x1FFFFu);
-              wbits[u][qd] = rr[qd] >> 17;
-            }
+            raw[u][0] = r.x;
+            raw[u][1] = r.y;
+            raw[u][2] = r.z;
+            raw[u][3] = r.w;
           } else {
             const uint4* p4 = reinterpret_cast<const uint4*>(static_cast<const uint2*>(P.syn) + slot);
             const uint4 r0 = __ldcs(p4);
             const uint4 r1 = __ldcs(p4 + 1);
-            code[u][0] = r0.x; wbits[u][0] = r0.y;
-            code[u][1] = r0.z; wbits[u][1] = r0.w;
-            code[u][2] = r1.x; wbits[u][2] = r1.y;
-            code[u][3] = r1.z; wbits[u][3] = r1.w;
+            raw[u][0] = r0.x; raw[u][1] = r0.y; raw[u][2] = r0.z; raw[u][3] = r0.w;
+            raw[u][4] = r1.x; raw[u][5] = r1.y; raw[u][6] = r1.z; raw[u][7] = r1.w;
           }
         }
       }
@@ -502,9 +496,16 @@ __device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item
 #pragma unroll
     for (int u = 0; u < INFL; ++u) {
 #pragma unroll
-      for (int qd = 0; qd < 4; ++qd)
-        deliver_record<PREC>(in[u] ? code[u][qd] : kPad, wbits[u][qd], inf[u], win_s, wbase, wlen,
-                             pol, nb, P);
+      for (int qd = 0; qd < 4; ++qd) {
+        if (PREC == SNN_EXACT_F16W) {
+          const uint32_t w = raw[u][qd];
+          deliver_record<PREC>(w == kPad ? kPad : (w & 0x1FFFFu), w >> 17, inf[u], win_s, wbase,
+                               wlen, pol, nb, P);
+        } else {
+          deliver_record<PREC>(raw[u][2 * qd], raw[u][2 * qd + 1], inf[u], win_s, wbase, wlen,
+                               pol, nb, P);
+        }
+      }
     }
   }
 }
@@ -674,7 +675,8 @@ __global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepPara
   __shared__ DeliverSmem S;
   __shared__ uint32_t s_nb[PREC == SNN_EXACT_F16W ? kNbEntries : 1];
   const long long t = P.ctl->t;
-  deliver_body<PREC, kInflight>(P, t, (int)blockIdx.x, (int)gridDim.x, S, s_win, s_nb);
+  deliver_body<PREC, PREC == SNN_EXACT_F16W ? kInflightF16 : kInflight>(
+      P, t, (int)blockIdx.x, (int)gridDim.x, S, s_win, s_nb);
 
   // the last block to finish closes the step
   __syncthreads();
