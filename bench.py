@@ -442,9 +442,13 @@ def _batched_form(snn, torch, stream, steps=2000, n_nets=64):
     b = snn.Batch(grids, neurons, synapses, seeds, "f32w", stream=stream.cuda_stream)
     torch.cuda.synchronize()
     out["build_s"] = time.perf_counter() - t0
-    out["tuned_choice"] = b.tune(25)
-    tuned_steps = 2 * 4 * 25
-    r0 = sum(m.stats()[0] for m in b.members)
+    choice = b.tune(25)
+    out["tuned_choice"] = choice
+    out["tuned_schedule"] = {"chunks_in_flight": [4, 4, 2, 2][choice % 4],
+                             "windows": choice % 2 == 0,
+                             "delivery_blocks_per_column": [8, 4, 2, 1][choice // 4]}
+    tuned_steps = 2 * 2 * 4 * 25  # two stages of two rounds of four candidates
+    r0 = [m.stats()[0] for m in b.members]
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -452,12 +456,17 @@ def _batched_form(snn, torch, stream, steps=2000, n_nets=64):
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    r1 = sum(m.stats()[0] for m in b.members)
+    r1 = [m.stats()[0] for m in b.members]
     b.close()
-    out["events_per_s"] = (r1 - r0) / (ms * 1e-3)
+    hbm, _ = _peaks()
+    alg = _batch_bytes(grids, neurons, synapses, [c - a for a, c in zip(r0, r1)], steps)
+    out["events_per_s"] = (sum(r1) - sum(r0)) / (ms * 1e-3)
     out["ms_per_step"] = ms / steps
+    out["algorithmic_bytes_per_step"] = alg / steps
+    out["step_gbs"] = alg / (ms * 1e-3) / 1e9
+    out["step_frac_hbm"] = out["step_gbs"] / hbm
     # the same nets, one by one, same steps after the same warm-up
-    total_ms, ev_seq = 0.0, 0.0
+    total_ms, ev_seq = 0.0, []
     for g, n, s, sd in zip(grids, neurons, synapses, seeds):
         net = snn.Net(g[0], g[1], n, s, sd, "f32w", stream=stream.cuda_stream)
         net.step(tuned_steps)
@@ -468,12 +477,28 @@ def _batched_form(snn, torch, stream, steps=2000, n_nets=64):
         ev1.record(stream)
         torch.cuda.synchronize()
         total_ms += ev0.elapsed_time(ev1)
-        ev_seq += net.stats()[0] - a0
+        ev_seq.append(net.stats()[0] - a0)
         net.close()
+    alg_seq = _batch_bytes(grids, neurons, synapses, ev_seq, steps)
     out["sequential_ms_per_step"] = total_ms / steps
-    out["sequential_events_per_s"] = ev_seq / (total_ms * 1e-3)
+    out["sequential_events_per_s"] = sum(ev_seq) / (total_ms * 1e-3)
+    out["sequential_step_gbs"] = alg_seq / (total_ms * 1e-3) / 1e9
     out["batch_speedup"] = total_ms / ms
     return out
+
+
+def _batch_bytes(grids, neurons, synapses, events, steps):
+    """Algorithmic bytes of `steps` steps of several FP32-weight nets with
+    `events` recurrent synaptic events each: per neuron and step 26 B (state
+    and input), per spike 12 B (list entry and record) + k_out 8-byte records
+    + 6 B per delay bucket (list entry and bucket end), as for one net."""
+    total = 0.0
+    for g, n, s, ev in zip(grids, neurons, synapses, events):
+        N = g[0] * g[1] * n["n_per_col"]
+        spikes = ev / s["k_out"]
+        ndel = s["d_max"] - s["d_min"] + 1
+        total += 26.0 * N * steps + spikes * (12.0 + 8.0 * s["k_out"] + 6.0 * ndel)
+    return total
 
 
 def _precision_form(snn, torch, stream, warmup, steps=1000):

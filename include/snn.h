@@ -276,10 +276,13 @@ snn_net* snn_batch_net(snn_batch* batch, int k);
 
 /*
  * snn_batch_tune -- pick the fastest delivery schedule for this batch (16-byte
- * chunks in flight per lane: 4 or 2; shared-memory windows: on or off) by
- * timing two interleaved rounds of steps_per_trial steps of each.  The trial
- * steps advance the simulation (all schedules compute identical sums).
- * *choice (may be NULL) receives the pick, 0..3.
+ * chunks in flight per lane: 4 or 2; shared-memory windows: on or off), then
+ * the fastest delivery density (8, 4, 2 or 1 virtual delivery blocks per
+ * member column, at most the member's standalone grid), each by timing two
+ * interleaved rounds of steps_per_trial steps of every candidate (16 trials
+ * in all).  The trial steps advance the simulation (every candidate computes
+ * identical sums).  *choice (may be NULL) receives the pick, schedule (0..3)
+ * + 4 x density index (0..3).
  */
 int snn_batch_tune(snn_batch* batch, int64_t steps_per_trial, int32_t* choice);
 

@@ -863,7 +863,9 @@ struct snn_batch {
   int precision = 0, num_sms = 0, max_npc = 0;
   int infl = 4;            // 16-byte chunks in flight in the delivery loop
   int agg = 1;             // block windows for the local half of the synapses
+  int dens8 = 64;          // delivery virtual blocks per 8 member columns
   int choice = -1;         // autotuner's pick (-1: not tuned)
+  std::vector<int> first;  // host copy of d_first
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   StepParams* d_nets = nullptr;
@@ -899,6 +901,27 @@ void batch_release(snn_batch* b) {
   if (b->d_first) cudaFree(b->d_first);
   if (b->d_bar) cudaFree(b->d_bar);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+// Delivery virtual blocks of member k: dens8 per 8 columns (at least one, at
+// most its standalone grid).  Any count gives the same sums (the items are
+// split into that many equal ranges).
+void batch_delivery_firsts(snn_batch* b) {
+  const size_t n = b->nets.size();
+  for (size_t k = 0; k < n; ++k) {
+    const snn_net* net = b->nets[k];
+    const long long dg =
+        std::min<long long>(net->deliver_grid, std::max<long long>(1, (long long)b->dens8 * net->ncol / 8));
+    b->first[(n + 1) + k + 1] = b->first[(n + 1) + k] + (int)dg;
+  }
+}
+
+// Upload the virtual-block tables (host copy in b->first).
+int batch_upload_firsts(snn_batch* b) {
+  SNN_BCUDA(b, cudaMemcpyAsync(b->d_first, b->first.data(), b->first.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, b->stream));
+  SNN_BCUDA(b, cudaStreamSynchronize(b->stream));
+  return SNN_OK;
 }
 
 // Upload the members' step parameters with the batch's window setting.
@@ -974,7 +997,7 @@ int snn_batch_build(int n_nets, const int32_t* grid_w, const int32_t* grid_h,
     b->own_stream = true;
   }
   int rc = SNN_OK;
-  std::vector<int> first(2 * (size_t)(n_nets + 1), 0);
+  b->first.assign(2 * (size_t)(n_nets + 1), 0);
   for (int k = 0; k < n_nets && rc == SNN_OK; ++k) {
     snn_net* net = nullptr;
     rc = snn_build(grid_w[k], grid_h[k], neuron + k, synapse + k, seeds[k], precision, b->stream,
@@ -984,11 +1007,8 @@ int snn_batch_build(int n_nets, const int32_t* grid_w, const int32_t* grid_h,
     b->nets.push_back(net);
     b->max_npc = std::max(b->max_npc, net->npc);
     b->num_sms = net->num_sms;
-    // update: the net's own grid (its partial sums and record regions);
-    // delivery: 8 virtual blocks per column, at most the standalone grid
-    first[k + 1] = first[k] + net->update_grid;
-    const long long dg = std::min<long long>(net->deliver_grid, std::max<long long>(1, 8 * net->ncol));
-    first[(n_nets + 1) + k + 1] = first[(n_nets + 1) + k] + (int)dg;
+    // update: the net's own grid (its partial sums and record regions)
+    b->first[k + 1] = b->first[k] + net->update_grid;
   }
   if (rc != SNN_OK) {
     const std::string why = g_err;
@@ -996,11 +1016,12 @@ int snn_batch_build(int n_nets, const int32_t* grid_w, const int32_t* grid_h,
     delete b;
     return bfail(nullptr, rc, why);
   }
+  batch_delivery_firsts(b);
   cudaError_t e = cudaMalloc(&b->d_nets, sizeof(StepParams) * (size_t)n_nets);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_first, first.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_first, b->first.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, 4 * sizeof(unsigned));
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_first, first.data(), first.size() * sizeof(int),
+    e = cudaMemcpyAsync(b->d_first, b->first.data(), b->first.size() * sizeof(int),
                         cudaMemcpyHostToDevice, b->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1034,40 +1055,56 @@ snn_net* snn_batch_net(snn_batch* b, int k) {
 int snn_batch_tune(snn_batch* b, int64_t steps_per_trial, int32_t* choice) {
   if (!b || steps_per_trial < 1) return bfail(b, SNN_EINVAL, "bad argument");
   // every variant computes the same sums, so the trials simply advance the
-  // simulation; two interleaved rounds even out changes in activity
+  // simulation; two interleaved rounds even out changes in activity.  Stage
+  // 0 times the four delivery schedules, stage 1 the delivery densities with
+  // the schedule that won.
   const int infl[4] = {4, 4, 2, 2}, agg[4] = {1, 0, 1, 0};
-  double ms[4] = {0, 0, 0, 0};
+  const int dens8[4] = {64, 32, 16, 8};  // 8, 4, 2 and 1 blocks per column
   cudaEvent_t e0, e1;
   SNN_BCUDA(b, cudaEventCreate(&e0));
   SNN_BCUDA(b, cudaEventCreate(&e1));
   int rc = SNN_OK;
-  for (int round = 0; round < 2 && rc == SNN_OK; ++round) {
-    for (int v = 0; v < 4 && rc == SNN_OK; ++v) {
-      b->infl = infl[v];
-      b->agg = agg[v];
+  int pick[2] = {0, 0};
+  for (int stage = 0; stage < 2 && rc == SNN_OK; ++stage) {
+    double ms[4] = {0, 0, 0, 0};
+    for (int round = 0; round < 2 && rc == SNN_OK; ++round) {
+      for (int v = 0; v < 4 && rc == SNN_OK; ++v) {
+        if (stage == 0) {
+          b->infl = infl[v];
+          b->agg = agg[v];
+          rc = batch_upload(b);
+        } else {
+          b->dens8 = dens8[v];
+          batch_delivery_firsts(b);
+          rc = batch_upload_firsts(b);
+        }
+        if (rc) break;
+        cudaEventRecord(e0, b->stream);
+        rc = batch_run(b, steps_per_trial);
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float x = 0.f;
+        cudaEventElapsedTime(&x, e0, e1);
+        ms[v] += x;
+      }
+    }
+    for (int v = 1; v < 4; ++v)
+      if (ms[v] < ms[pick[stage]]) pick[stage] = v;
+    if (rc == SNN_OK && stage == 0) {
+      b->infl = infl[pick[0]];
+      b->agg = agg[pick[0]];
       rc = batch_upload(b);
-      if (rc) break;
-      cudaEventRecord(e0, b->stream);
-      rc = batch_run(b, steps_per_trial);
-      cudaEventRecord(e1, b->stream);
-      cudaEventSynchronize(e1);
-      float x = 0.f;
-      cudaEventElapsedTime(&x, e0, e1);
-      ms[v] += x;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != SNN_OK) return rc;
-  int best = 0;
-  for (int v = 1; v < 4; ++v)
-    if (ms[v] < ms[best]) best = v;
-  b->infl = infl[best];
-  b->agg = agg[best];
-  b->choice = best;
-  rc = batch_upload(b);
+  b->dens8 = dens8[pick[1]];
+  batch_delivery_firsts(b);
+  rc = batch_upload_firsts(b);
   if (rc) return rc;
-  if (choice) *choice = best;
+  b->choice = pick[0] + 4 * pick[1];
+  if (choice) *choice = b->choice;
   return SNN_OK;
 }
 

@@ -30,3 +30,19 @@ def test_single_thread_leg_reports_both(orc):
     cb = bench._cpu_baseline("cols2x2_f32w", seconds_target=0.3)
     assert cb["cores"] == 1 and cb["value"] > 0 and cb["kind"] == "oracle"
     assert cb["all_cores"] is not None and cb["all_cores"]["cores"] >= 1
+
+
+def test_batch_bytes_match_the_per_net_formula():
+    """The batched form's algorithmic bytes: 26 B per neuron and step, and per
+    spike 12 B + k_out records of 8 B + 6 B per delay bucket, summed over nets."""
+    import bench
+    from paper_1511_09325_gb300 import workloads as W
+
+    grids = [(1, 1), (2, 3)]
+    neurons = [W.neuron_params(), W.neuron_params(nu_ext_kHz=3.0)]
+    synapses = [W.synapse_params(), W.synapse_params(k_out=150, d_min=2, d_max=7)]
+    events = [1240.0 * 10, 150.0 * 4]  # 10 and 4 spikes
+    got = bench._batch_bytes(grids, neurons, synapses, events, 5)
+    want = (26 * 1240 * 5 + 10 * (12 + 8 * 1240 + 6 * 20)
+            + 26 * 6 * 1240 * 5 + 4 * (12 + 8 * 150 + 6 * 6))
+    assert got == want
