@@ -287,10 +287,11 @@ def _kernel_roofline(snn, torch, cfg, seed, stream, warmup, P, workload):
             "algorithmic_bytes_per_launch": {"update": kbytes[0] / P, "deliver": kbytes[1] / P}}
 
 
-def _e2e(net, torch, E, ws):
+def _e2e(net, torch, E, dist=None, device="cuda"):
     """Same metric through the public API with host buffers: every step is
     one snn_step call followed by one drain of that step's spike records into
-    host arrays (device -> host copies and stream sync inside the region)."""
+    host arrays (device -> host copies and stream sync inside the region).
+    With several ranks: the events of all ranks over the slowest rank's time."""
     import numpy as np
 
     net.spikes()
@@ -306,7 +307,10 @@ def _e2e(net, torch, E, ws):
         d2h += 8 * n + 16  # records, plus the drain header
     dt = time.perf_counter() - t0
     r1, _, _ = net.stats()
-    return {"value": (r1 - r0) * ws / dt, "unit": UNIT, "h2d_bytes_per_step": 0,
+    ms, ev = dt * 1e3, r1 - r0
+    if dist:
+        ms, ev, _ = reduce_ranks(dist, ms, ev, 0.0, device)
+    return {"value": ev / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 0,
             "d2h_bytes_per_step": d2h / E, "steps": E}
 
 
@@ -350,7 +354,7 @@ def run_ours(args):
         ms, rec_ev, ext_ev = reduce_ranks(dist, ms, rec_ev, ext_ev, "cuda")
     info = net.info()
     _, pop_hz = net.rates()
-    e2e = _e2e(net, torch, max(1, min(args.e2e_steps, max(K, 1))), ws)
+    e2e = _e2e(net, torch, max(1, min(args.e2e_steps, max(K, 1))), dist)
     net.close()
     P = K if args.profile_steps is None else min(args.profile_steps, K)
     roofline = _kernel_roofline(snn, torch, cfg, seed, stream, Wm, max(1, P), args.workload)

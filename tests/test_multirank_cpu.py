@@ -100,3 +100,53 @@ def test_bench_reduction_over_replicas(tmp_path):
     for r in range(2):
         ms, rec, ext = np.load(tmp_path / ("red%d.npy" % r))
         assert ms == 11.0 and rec == 300.0 and ext == 14.0
+
+
+class _SleepyNet:
+    """Stands in for a net in bench._e2e: each step takes `dt` seconds and
+    adds `ev` recurrent events; a read drains nothing."""
+
+    def __init__(self, dt, ev):
+        self.n, self.dt, self.ev, self.events = 4, dt, ev, 0.0
+
+    def spikes(self):
+        return None
+
+    def step(self, k):
+        import time
+
+        time.sleep(self.dt * k)
+        self.events += self.ev * k
+
+    def spikes_into(self, steps, ids):
+        return 0, False
+
+    def stats(self):
+        return self.events, 0.0, 0
+
+
+class _NoCuda:
+    class cuda:
+        @staticmethod
+        def synchronize():
+            pass
+
+
+def _e2e_worker(rank, world, port, out_dir):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    dist = _init(rank, world, port)
+    net = _SleepyNet(0.01 * (rank + 1), 100.0 * (rank + 1))
+    r = bench._e2e(net, _NoCuda, 3, dist, "cpu")
+    np.save(os.path.join(out_dir, "e2e%d.npy" % rank), np.array([r["value"]]))
+    dist.destroy_process_group()
+
+
+def test_bench_e2e_is_whole_job_over_ranks(tmp_path):
+    """The end-to-end rate of N ranks is the events of all ranks (here 300 +
+    600) over the slowest rank's time (3 steps of 20 ms), on every rank."""
+    mp.spawn(_e2e_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    v = [float(np.load(tmp_path / ("e2e%d.npy" % r))[0]) for r in range(2)]
+    assert v[0] == v[1]
+    assert 900.0 / 0.5 < v[0] <= 900.0 / 0.06
