@@ -109,3 +109,58 @@ def test_gradient_entry_points_refuse_null_arguments(lib):
     assert lib.snn_grad_run(None, None, ctypes.byref(loss), None, None) == snn.SNN_EINVAL
     assert lib.snn_grad_last_error(None) == b""
     lib.snn_grad_destroy(None)
+
+
+def test_batch_entry_points_validate_before_touching_a_device(lib):
+    import ctypes
+
+    grids = [(2, 2), (1, 1)]
+    good_n, good_s = [W.neuron_params()] * 2, [W.synapse_params()] * 2
+    # no nets, too many nets, a bad member: refused before any stream exists
+    for grids_, ns, ss in (([], [], []), ([(1, 1)] * 257, [W.neuron_params()] * 257,
+                                          [W.synapse_params()] * 257),
+                           (grids, [W.neuron_params(), W.neuron_params(n_exc=5000)], good_s),
+                           (grids, good_n, [W.synapse_params(), W.synapse_params(d_min=0)])):
+        with pytest.raises(snn.SnnError) as e:
+            snn.Batch(grids_, ns, ss, list(range(len(grids_))))
+        assert e.value.code == snn.SNN_EINVAL
+    with pytest.raises(snn.SnnError) as e:
+        snn.Batch([(0, 3)], [W.neuron_params()], [W.synapse_params()], [1])
+    assert e.value.code == snn.SNN_EINVAL
+    out = ctypes.c_void_p()
+    assert lib.snn_batch_build(1, None, None, None, None, None, 0, None,
+                               ctypes.byref(out)) == snn.SNN_EINVAL
+    assert out.value is None
+    assert lib.snn_batch_build(1, None, None, None, None, None, 0, None, None) == snn.SNN_EINVAL
+    assert lib.snn_batch_step(None, 1) == snn.SNN_EINVAL
+    assert lib.snn_batch_tune(None, 1, None) == snn.SNN_EINVAL
+    assert lib.snn_batch_set_wait(None, 1, 0) == snn.SNN_EINVAL
+    assert lib.snn_batch_net(None, 0) is None
+    assert lib.snn_batch_last_error(None)  # the last refusal's message
+    lib.snn_batch_destroy(None)
+
+
+def test_noalloc_update_validates_before_touching_a_device(lib):
+    import numpy as np
+
+    n = W.neuron_params()
+    buf = np.zeros(64, np.float32)
+    p = buf.ctypes.data  # 16-byte aligned host memory: never dereferenced here
+
+    def call(**kw):
+        a = dict(grid_w=1, grid_h=1, neuron=n, seed=1, step=0, v=p, c=p, refractory=p,
+                 input_fx=p, spikes=p)
+        a.update(kw)
+        with pytest.raises(snn.SnnError) as e:
+            snn.snn_update_noalloc(**a)
+        return e.value.code
+
+    assert call(neuron=W.neuron_params(n_exc=2000)) == snn.SNN_EINVAL
+    assert call(grid_w=0) == snn.SNN_EINVAL
+    assert call(grid_w=129, grid_h=128) == snn.SNN_EINVAL  # 16 512 columns > 16 384
+    assert call(step=-1) == snn.SNN_EINVAL
+    assert call(step=1 << 32) == snn.SNN_EINVAL
+    assert call(v=None) == snn.SNN_EINVAL
+    assert call(spikes=None) == snn.SNN_EINVAL
+    assert call(v=p + 4) == snn.SNN_EINVAL  # V must be 16-byte aligned
+    assert call(refractory=p + 2) == snn.SNN_EINVAL  # refractory must be 4-byte aligned
