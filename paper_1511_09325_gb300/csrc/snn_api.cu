@@ -526,21 +526,18 @@ int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes) 
     e = cudaMemcpyAsync(hspk.data(), dspk, hspk.size() * 8, cudaMemcpyDeviceToHost, net->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
   double t_up = 0.0, t_dl = 0.0, b_up = 0.0, b_dl = 0.0;
-  if (e == cudaSuccess) {
-    const double neuron_bytes = 26.0 * (double)net->N;
-    for (int64_t s = 0; s < n_steps; ++s) {
-      float a = 0.f, b = 0.f;
-      cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
-      cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]);
-      t_up += a;
-      t_dl += b;
-      const double S = (double)(hspk[s + 1] - hspk[s]);
-      b_up += neuron_bytes + 12.0 * S;
-      b_dl += S * ((double)net->total_syn / (double)net->N * net->rec_size + 6.0 * net->ndel);
-    }
-  } else {
-    rc = cuda_fail(net, e, "profiled step");
+  const double neuron_bytes = 26.0 * (double)net->N;
+  for (int64_t s = 0; s < n_steps && e == cudaSuccess; ++s) {
+    float a = 0.f, b = 0.f;
+    e = cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]);
+    t_up += a;
+    t_dl += b;
+    const double S = (double)(hspk[s + 1] - hspk[s]);
+    b_up += neuron_bytes + 12.0 * S;
+    b_dl += S * ((double)net->total_syn / (double)net->N * net->rec_size + 6.0 * net->ndel);
   }
+  if (e != cudaSuccess) rc = cuda_fail(net, e, "profiled step");
   for (size_t i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
   cudaFree(dspk);
   if (rc == SNN_OK) {
@@ -1060,9 +1057,13 @@ int snn_batch_tune(snn_batch* b, int64_t steps_per_trial, int32_t* choice) {
   // the schedule that won.
   const int infl[4] = {4, 4, 2, 2}, agg[4] = {1, 0, 1, 0};
   const int dens8[4] = {64, 32, 16, 8};  // 8, 4, 2 and 1 blocks per column
-  cudaEvent_t e0, e1;
-  SNN_BCUDA(b, cudaEventCreate(&e0));
-  SNN_BCUDA(b, cudaEventCreate(&e1));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return bfail(b, SNN_ECUDA, std::string("tuner events: ") + cudaGetErrorString(ce));
+  }
   int rc = SNN_OK;
   int pick[2] = {0, 0};
   for (int stage = 0; stage < 2 && rc == SNN_OK; ++stage) {
@@ -1079,12 +1080,19 @@ int snn_batch_tune(snn_batch* b, int64_t steps_per_trial, int32_t* choice) {
           rc = batch_upload_firsts(b);
         }
         if (rc) break;
-        cudaEventRecord(e0, b->stream);
-        rc = batch_run(b, steps_per_trial);
-        cudaEventRecord(e1, b->stream);
-        cudaEventSynchronize(e1);
+        cudaError_t e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) {
+          rc = batch_run(b, steps_per_trial);
+          if (rc) break;
+          e = cudaEventRecord(e1, b->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float x = 0.f;
-        cudaEventElapsedTime(&x, e0, e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
+        if (e != cudaSuccess) {
+          rc = bfail(b, SNN_ECUDA, std::string("tuner timing: ") + cudaGetErrorString(e));
+          break;
+        }
         ms[v] += x;
       }
     }
