@@ -25,6 +25,13 @@
  *
  * Compile with -ffp-contract=off: every float operation is spelled out and
  * must not be fused by the compiler.
+ *
+ * Pins (tests, no GPU): Philox known-answer vectors; the quantile, Poisson and
+ * propagator tables against library routines; closed forms of the
+ * sub-threshold and constant-drive dynamics; construction invariants and
+ * Table 1 sizes; whole networks against a dense per-delay restatement, bit
+ * for bit.  Parity unpinned by the paper: the network's firing rates, which
+ * it does not print.
  */
 #include <math.h>
 #include <stdint.h>

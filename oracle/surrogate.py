@@ -31,6 +31,12 @@ surrogate-gradient extension of the Sec. 2 network, in plain numpy/scipy:
 the reverse-mode recursion (adjoint of every line above, in reverse order),
 written out by hand; the adjoint of the delayed delivery is the transposed
 matrix product, i.e. a gather over each neuron's outgoing synapses.
+
+Pins (tests, no GPU): soft-mode gradient = central finite differences; the
+beta -> infinity limit = the spiking C oracle's raster; reverse recursion =
+forward-mode tangents in both modes.  The hard mode's surrogate derivative
+itself is a choice, not a derivative of the forward: the paper has no
+gradient to compare with (parity unpinned by the paper).
 """
 import numpy as np
 import scipy.sparse as sp

@@ -9,7 +9,9 @@ things other than itself:
   - its forward pass, in the limit of a step-like sigmoid and with the
     spiking model's Poisson input, against the independent C oracle of the
     spiking network (same raster, same final potentials);
-  - the exact-FP32 forward against the FP64 one (same spikes).
+  - the exact-FP32 forward against the FP64 one (same spikes);
+  - its reverse recursion against forward-mode tangents of the same step, in
+    hard mode (where finite differences do not apply) and in soft mode.
 """
 import numpy as np
 import pytest
@@ -106,3 +108,81 @@ def test_fp32_forward_has_the_fp64_spikes(net1):
     assert l64 == l32
     g64, g32 = net1.backward(s64), net1.backward(s32)
     assert np.allclose(g32, g64, rtol=1e-3, atol=1e-6 * np.abs(g64).max())
+
+
+def _forward_mode(net, theta, T, beta=5.0, targets=(3.0, 8.0), hard=True):
+    """Loss and its six derivatives by forward-mode accumulation: each state
+    variable carries its tangent with respect to every parameter (arrays of
+    6 x N) through the step, with ds/dU taken as the fast-sigmoid surrogate
+    (hard spikes) or the sigmoid's own derivative (soft).  The refractory gate
+    max(0, 1 - s(t-1) - s(t-2)) passes tangents only where it is positive.
+    This accumulates the derivative in the opposite direction to the oracle's
+    hand-written adjoint recursion, so the two agree only if every adjoint
+    there is the transpose of the corresponding step here."""
+    p, N, D, exc = net.p, net.N, net.D, net.exc
+    aEE, aEI, aIE, aII, gc, nu = (float(x) for x in theta)
+    aE, aI = np.where(exc, aEE, aEI), np.where(exc, aIE, aII)
+    daE, daI, dpvc = np.zeros((6, N)), np.zeros((6, N)), np.zeros((6, N))
+    daE[0], daE[1] = exc, ~exc
+    daI[2], daI[3] = exc, ~exc
+    dpvc[4] = np.where(exc, net.kappa, 0.0)
+    h = float(p.h)
+    lam = nu * h
+    J = float(np.float32(p.j_ext))
+    vr, th, dc = (float(np.float32(x)) for x in (p.v_reset, p.theta, p.dc))
+    pvc = np.where(exc, gc * net.kappa, float(np.float32(p.gc_inh)) * net.kappa)
+    xi = oracle.surr_xi(p, 0, N, 0, T)
+    hist, dhist = np.zeros((D, N)), np.zeros((D, 6, N))
+    s1, s2 = np.zeros(N), np.zeros(N)
+    ds1, ds2 = np.zeros((6, N)), np.zeros((6, N))
+    V, c = net.v0.copy(), np.zeros(N)
+    dV, dc_ = np.zeros((6, N)), np.zeros((6, N))
+    sums, dsums = np.zeros(2), np.zeros((2, 6))
+    for t in range(T):
+        XE, XI = net.M["E"] @ hist.reshape(-1), net.M["I"] @ hist.reshape(-1)
+        dstk = dhist.transpose(1, 0, 2).reshape(6, D * N)
+        dXE, dXI = (net.M["E"] @ dstk.T).T, (net.M["I"] @ dstk.T).T
+        I = aE * XE + aI * XI + J * (lam + np.sqrt(lam) * xi[t])
+        dI = daE * XE + aE * dXE + daI * XI + aI * dXI
+        dI[5] += J * h * (1.0 + xi[t] / (2.0 * np.sqrt(lam)))
+        gate = 1.0 - s1 - s2
+        g = np.maximum(gate, 0.0)
+        dg = np.where(gate > 0, -(ds1 + ds2), 0.0)
+        U = g * (V + I) + (1.0 - g) * vr
+        dU = dg * (V + I - vr) + g * (dV + dI)
+        if hard:
+            s = (U >= th).astype(np.float64)
+            slope = 1.0 / (1.0 + beta * np.abs(U - th)) ** 2
+        else:
+            s = 1.0 / (1.0 + np.exp(-beta * (U - th)))
+            slope = beta * s * (1.0 - s)
+        ds = slope * dU
+        Vp, dVp = U - s * (U - vr), (1.0 - s) * dU - ds * (U - vr)
+        cp, dcp = c + dc * s, dc_ + dc * ds
+        V, dV = net.pvv * Vp + pvc * cp, net.pvv * dVp + pvc * dcp + dpvc * cp
+        c, dc_ = net.pcc * cp, net.pcc * dcp
+        hist[1:], dhist[1:] = hist[:-1].copy(), dhist[:-1].copy()
+        hist[0], dhist[0] = s, ds
+        s1, s2, ds1, ds2 = s, s1, ds, ds1
+        sums += (s[exc].sum(), s[~exc].sum())
+        dsums += (ds[:, exc].sum(1), ds[:, ~exc].sum(1))
+    n = np.array([exc.sum(), N - exc.sum()], np.float64)
+    r = 1000.0 * sums / (T * n)
+    loss = float(((r - np.array(targets)) ** 2).sum())
+    dloss = (2.0 * (r - np.array(targets)) * 1000.0 / (T * n)) @ dsums
+    return loss, dloss
+
+
+@pytest.mark.parametrize("hard,T", [(True, 40), (False, 10)])
+def test_reverse_gradient_equals_forward_mode_tangents(net1, hard, T):
+    """The hard mode's surrogate gradient has no finite-difference check (the
+    spiking loss is piecewise constant), so its adjoint recursion is pinned
+    against forward-mode tangents of the same linearised step: all six
+    derivatives agree to FP64 rounding.  Soft spikes too, for the record."""
+    loss, st = net1.forward(THETA, T, hard=hard)
+    g = net1.backward(st)
+    lf, gf = _forward_mode(net1, THETA, T, hard=hard)
+    assert lf == pytest.approx(loss, rel=1e-12)
+    assert st["s"].sum() > 100  # spikes (or spike mass) on the path
+    scale = np.abs(gf).max()
+    assert np.all(np.abs(g - gf) <= 1e-9 * np.maximum(np.abs(gf), 1e-3 * scale)), (g, gf)
