@@ -46,3 +46,27 @@ def test_batch_bytes_match_the_per_net_formula():
     want = (26 * 1240 * 5 + 10 * (12 + 8 * 1240 + 6 * 20)
             + 26 * 6 * 1240 * 5 + 4 * (12 + 8 * 150 + 6 * 6))
     assert got == want
+
+
+def test_clock_samples_parse_median_max_and_reasons():
+    """nvidia-smi lines (uuid, SM MHz, max MHz, power, active mask, then the
+    four throttle flags): the median clock under load, the maximum, the
+    reasons that were ever active, other GPUs' and garbled lines ignored."""
+    import bench
+
+    u = "GPU-0a1b2c3d-4e5f-6789-abcd-ef0123456789"
+    other = "GPU-ffffffff-0000-0000-0000-000000000000"
+    na = "Not Active"
+    lines = [
+        "%s, 1995, 2070, 880.1, 0x0, %s, %s, %s, %s" % (u, na, na, na, na),
+        "%s, 2070, 2070, 910.0, 0x4, %s, %s, %s, Active" % (u, na, na, na),
+        "%s, 2025, 2070, 905.2, 0x0, %s, %s, %s, %s" % (u, na, na, na, na),
+        "%s, 705, 2070, 90.0, 0x8, Active, %s, %s, %s" % (other, na, na, na),
+        "%s, [N/A], 2070, 0, 0x0, %s, %s, %s, %s" % (u, na, na, na, na),
+        "garbage",
+    ]
+    r = bench.parse_clocks("\n".join(lines), u)
+    assert r == {"sm_mhz": 2025.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+    assert bench.parse_clocks("", u) is None
+    assert bench.parse_clocks("\n".join(lines))["samples"] == 4  # every GPU's lines
