@@ -136,6 +136,31 @@ def parse_clocks(text, uuid=""):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def clocks_rejected(clk, floor=0.85):
+    """True when a clock record disqualifies the timing it covers: a hardware
+    or thermal slowdown was active, or the median SM clock sat below `floor`
+    of its maximum with no reason given (a clock lock left by someone else).
+    A power cap alone is kept (and shows in the record)."""
+    if not clk:
+        return False
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if bad & set(clk["reasons"]):
+        return True
+    return not clk["reasons"] and clk["sm_mhz"] < floor * clk["sm_max_mhz"]
+
+
+def any_rank(dist, flag, device):
+    """The flag of every rank or-ed together (so that all ranks take the same
+    branch around a collective)."""
+    if not dist:
+        return bool(flag)
+    import torch
+
+    t = torch.tensor([1 if flag else 0], device=device, dtype=torch.int32)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return bool(t.item())
+
+
 def _cpu_baseline(workload, seconds_target=15.0):
     """The oracle, as it stands, on a bounded sample of the workload."""
     import oracle
@@ -357,6 +382,14 @@ def run_ours(args):
     net.spikes()
     ms, rec_ev, ext_ev = _timed(net, torch, stream, K, dist.barrier if dist else None)
     clk = clocks.stop()
+    if any_rank(dist, clocks_rejected(clk), "cuda"):
+        # a slowed or locked clock disqualifies the window: time the next one
+        clocks = Clocks(uuid)
+        clocks.start()
+        ms, rec_ev, ext_ev = _timed(net, torch, stream, K, dist.barrier if dist else None)
+        clk = clocks.stop()
+        if clk is not None:
+            clk["remeasured"] = True
     if dist:
         ms, rec_ev, ext_ev = reduce_ranks(dist, ms, rec_ev, ext_ev, "cuda")
     info = net.info()

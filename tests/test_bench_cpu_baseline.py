@@ -70,3 +70,16 @@ def test_clock_samples_parse_median_max_and_reasons():
                  "samples": 3}
     assert bench.parse_clocks("", u) is None
     assert bench.parse_clocks("\n".join(lines))["samples"] == 4  # every GPU's lines
+
+
+def test_clock_records_that_disqualify_a_timing():
+    import bench
+
+    ok = {"sm_mhz": 2025.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 9}
+    assert not bench.clocks_rejected(ok)
+    assert not bench.clocks_rejected(None)
+    assert not bench.clocks_rejected(dict(ok, reasons=["sw_power_cap"], sm_mhz=1500.0))
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected(dict(ok, reasons=[r]))
+    assert bench.clocks_rejected(dict(ok, sm_mhz=1200.0))  # locked low, no reason
+    assert not bench.any_rank(None, False, "cpu") and bench.any_rank(None, True, "cpu")

@@ -150,3 +150,21 @@ def test_bench_e2e_is_whole_job_over_ranks(tmp_path):
     v = [float(np.load(tmp_path / ("e2e%d.npy" % r))[0]) for r in range(2)]
     assert v[0] == v[1]
     assert 900.0 / 0.5 < v[0] <= 900.0 / 0.06
+
+
+def _any_rank_worker(rank, world, port, out_dir):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    dist = _init(rank, world, port)
+    got = [bench.any_rank(dist, rank == 1, "cpu"), bench.any_rank(dist, False, "cpu")]
+    np.save(os.path.join(out_dir, "any%d.npy" % rank), np.array(got))
+    dist.destroy_process_group()
+
+
+def test_bench_remeasure_decision_is_taken_by_all_ranks(tmp_path):
+    """One rank's disqualified clock record makes every rank time again (the
+    timed region holds barriers, so the ranks must take the same branch)."""
+    mp.spawn(_any_rank_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        assert list(np.load(tmp_path / ("any%d.npy" % r))) == [True, False]
