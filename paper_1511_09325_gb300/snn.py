@@ -173,8 +173,18 @@ def snn_read_spikes(handle, cap=None):
     return st[:n.value], ids[:n.value], rc == SNN_EOVERFLOW
 
 
+def _int32_out(a, name):
+    """A caller's output array must be writeable, C-contiguous int32: the
+    library writes that many int32 values through its pointer."""
+    if not (isinstance(a, np.ndarray) and a.dtype == np.int32 and a.flags.c_contiguous
+            and a.flags.writeable):
+        raise TypeError("%s must be a writeable C-contiguous int32 numpy array" % name)
+
+
 def snn_read_spikes_into(handle, steps, ids):
     """Drain into preallocated int32 arrays; returns (count, overflowed)."""
+    _int32_out(steps, "steps")
+    _int32_out(ids, "ids")
     n = ctypes.c_int64()
     rc = _check(load().snn_read_spikes(handle, _p(steps), _p(ids), int(min(len(steps), len(ids))),
                                        ctypes.byref(n)), handle, ok=(SNN_OK, SNN_EOVERFLOW))

@@ -164,3 +164,20 @@ def test_noalloc_update_validates_before_touching_a_device(lib):
     assert call(spikes=None) == snn.SNN_EINVAL
     assert call(v=p + 4) == snn.SNN_EINVAL  # V must be 16-byte aligned
     assert call(refractory=p + 2) == snn.SNN_EINVAL  # refractory must be 4-byte aligned
+
+
+def test_spike_readback_refuses_unsafe_output_arrays(lib):
+    """The library writes int32 records through the arrays' pointers, so a
+    wrong dtype, a strided view or a read-only array is refused before the
+    call (the handle is never used)."""
+    import numpy as np
+
+    good = np.zeros(8, np.int32)
+    ro = np.zeros(8, np.int32)
+    ro.flags.writeable = False
+    for bad in (np.zeros(8, np.int16), np.zeros(8, np.int64), np.zeros(16, np.int32)[::2], ro,
+                [0] * 8):
+        with pytest.raises(TypeError):
+            snn.snn_read_spikes_into(None, bad, good)
+        with pytest.raises(TypeError):
+            snn.snn_read_spikes_into(None, good, bad)
