@@ -124,7 +124,12 @@ int snn_build(int grid_w, int grid_h, const snn_neuron_params* neuron,
 /*
  * snn_step -- advance n_steps 1 ms steps (Sec. 1: fixed network step, spikes
  * delivered event by event).  Asynchronous on the net's stream: the steps run
- * as replays of a captured CUDA graph.  n_steps >= 0.
+ * as replays of a captured CUDA graph.  n_steps >= 0.  A delivery that finds
+ * its item counts disagreeing with the step's spike lists delivers nothing
+ * for the disagreeing part and sets the net's status word; from then on
+ * snn_step, snn_read_spikes, snn_read_rates and snn_stats return SNN_ESTATE
+ * (snn_step as soon as the status has reached the host, the reads after
+ * their synchronisation), and the net should be destroyed.
  */
 int snn_step(snn_net* net, int64_t n_steps);
 
@@ -185,7 +190,9 @@ int snn_row_lengths(snn_net* net, int64_t j0, int64_t n, int32_t* counts);
 /*
  * snn_info -- sizes of the net: info[0] = N neurons, [1] = synapses,
  * [2] = device bytes held, [3] = bytes of the synapse table, [4] = row
- * capacity in synapse slots, [5] = precision.  n = entries available.
+ * capacity in synapse slots, [5] = precision, [6] = side of the delivery
+ * tiles in columns, [7] = delivery blocks, [8] = update blocks.  n = entries
+ * available (at most 9 are written).
  */
 int snn_info(snn_net* net, int64_t* info, int n);
 

@@ -19,6 +19,7 @@ struct snn_net {
   int precision = 0, rowcap = 0, rec_size = 0, num_sms = 0, update_grid = 0;
   bool agg = true;
   int deliver_grid = 0;
+  int tile = 1, ring = 1, win_cap = 0, desc_words = 8;  // delivery tiles and windows
   long long N = 0, Npad = 0, ncol = 0;
   uint64_t seed = 0;
   snn_neuron_params neuron{};
@@ -31,7 +32,11 @@ struct snn_net {
   float* C = nullptr;
   uint8_t* R = nullptr;
   int32_t* acc = nullptr;
-  uint32_t* ids = nullptr;
+  uint32_t* desc = nullptr;               // spike descriptors
+  uint32_t* vcol = nullptr;               // delivery order of the columns
+  uint32_t* colv = nullptr;
+  unsigned* hstatus = nullptr;            // status word (pinned, mapped)
+  unsigned* hstatus_dev = nullptr;
   unsigned* cnt = nullptr;
   unsigned* ccnt = nullptr;
   uint32_t* deg = nullptr;                 // out-degree per neuron (paper law)
@@ -144,8 +149,9 @@ void release(snn_net* net) {
   if (net->hhdr) cudaFreeHost(net->hhdr);
   if (net->hmap) cudaFreeHost(net->hmap);
   if (net->hstage) cudaFreeHost(net->hstage);
+  if (net->hstatus) cudaFreeHost(net->hstatus);
   void* ptrs[] = {net->syn, net->bend, net->V, net->C, net->R, net->acc,
-                  net->ids, net->cnt, net->ccnt, net->deg, net->syn_part, net->isum, net->gsum, net->ctl, net->rec, net->rcnt, net->stage, net->dhdr, net->colcnt,
+                  net->desc, net->vcol, net->colv, net->cnt, net->ccnt, net->deg, net->syn_part, net->isum, net->gsum, net->ctl, net->rec, net->rcnt, net->stage, net->dhdr, net->colcnt,
                   net->ext_part, net->spk_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -192,6 +198,57 @@ int validate(int gw, int gh, const snn_neuron_params* n, const snn_synapse_param
   return SNN_OK;
 }
 
+// min(floor(2^32 / d), 2^32 - 1): the multiplier of the kernels' divisions.
+uint32_t recip32(uint32_t d) {
+  const unsigned long long m = (1ull << 32) / (unsigned long long)d;
+  return m > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)m;
+}
+
+// Delivery tiles: the largest square tile (side <= kMaxTile) whose window --
+// the tile plus a ring of one column, clipped to the grid -- fits the shared
+// memory budget of a delivery block.
+constexpr size_t kWindowBudget = 196 * 1024;
+
+void choose_tiles(snn_net* net) {
+  net->ring = 1;
+  int t = std::min(kMaxTile, std::max(net->W, net->H));
+  for (; t > 1; --t) {
+    const size_t ww = (size_t)std::min(t + 2 * net->ring, net->W);
+    const size_t wh = (size_t)std::min(t + 2 * net->ring, net->H);
+    if (ww * wh * (size_t)net->npc * 4 <= kWindowBudget) break;
+  }
+  net->tile = t;
+  const long long ww = std::min(t + 2 * net->ring, net->W);
+  const long long wh = std::min(t + 2 * net->ring, net->H);
+  net->win_cap = (int)((ww * wh * net->npc + 3) / 4 * 4);
+}
+
+// Virtual (delivery) order of the columns: tile by tile, tiles and the
+// columns inside a tile in row-major order.  vcol[v] = real column.
+void column_order(int W, int H, int T, std::vector<uint32_t>* vcol, std::vector<uint32_t>* colv) {
+  vcol->assign((size_t)W * H, 0u);
+  colv->assign((size_t)W * H, 0u);
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      const int tr = y / T, tc = x / T;
+      const int th = std::min(T, H - tr * T), tw = std::min(T, W - tc * T);
+      const long long v = (long long)tr * T * W + (long long)tc * th * T +
+                          (long long)(y - tr * T) * tw + (x - tc * T);
+      const uint32_t c = (uint32_t)(y * W + x);
+      (*vcol)[(size_t)v] = c;
+      (*colv)[c] = (uint32_t)v;
+    }
+}
+
+// A kernel found inconsistent counts: the net's stepping is no longer exact.
+int check_status(snn_net* net) {
+  if (net->hstatus && *reinterpret_cast<volatile unsigned*>(net->hstatus) != 0u)
+    return fail(net, SNN_ESTATE,
+                "a delivery found item counts that disagree with the spike lists; the net's "
+                "state is no longer exact");
+  return SNN_OK;
+}
+
 int capture(snn_net* net, int steps, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   SNN_CUDA(net, cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
@@ -227,6 +284,12 @@ void fill_step_params(snn_net* net) {
   p.rowcap = net->rowcap;
   p.ncol = (int)net->ncol;
   p.agg = net->agg ? 1 : 0;
+  p.tile = net->tile;
+  p.ring = net->ring;
+  p.win_cap = net->win_cap;
+  p.desc_words = net->desc_words;
+  p.npc_m = recip32((uint32_t)net->npc);
+  p.w_m = recip32((uint32_t)net->W);
   p.seed_lo = (uint32_t)(net->seed & 0xFFFFFFFFu);
   p.seed_hi = (uint32_t)(net->seed >> 32);
   p.pvv = t.pvv;
@@ -242,7 +305,11 @@ void fill_step_params(snn_net* net) {
   p.C = net->C;
   p.R = net->R;
   p.acc = net->acc;
-  p.ids = net->ids;
+  p.ids = nullptr;
+  p.desc = net->desc;
+  p.vcol = net->vcol;
+  p.colv = net->colv;
+  p.hstatus = net->hstatus_dev;
   p.cnt = net->cnt;
   p.ccnt = net->ccnt;
   p.deg = net->deg;
@@ -292,7 +359,11 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   SNN_CUDA(net, cudaGetDevice(&dev));
   SNN_CUDA(net, cudaDeviceGetAttribute(&net->num_sms, cudaDevAttrMultiProcessorCount, dev));
   net->update_grid = update_grid(net->N, net->num_sms);
-  net->deliver_grid = deliver_grid(precision, net->num_sms, net->npc, net->agg);
+  choose_tiles(net);
+  net->desc_words = net->ndel <= 28 ? 8 : 16;
+  fill_step_params(net);
+  net->deliver_grid = deliver_grid(net->sp, precision, net->num_sms);
+  if (net->deliver_grid < 1) return fail(net, SNN_ECUDA, "delivery kernel does not fit on the device");
   net->rec_region = (net->rec_cap + net->update_grid - 1) / net->update_grid;
 
   net->connectivity = sp->connectivity;
@@ -355,7 +426,9 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if ((rc = dalloc(net, &net->C, (size_t)net->Npad * 4))) return rc;
   if ((rc = dalloc(net, &net->R, (size_t)net->Npad))) return rc;
   if ((rc = dalloc(net, &net->acc, (size_t)net->Npad * 4))) return rc;
-  if ((rc = dalloc(net, &net->ids, (size_t)net->nslot * net->N * 4))) return rc;
+  if ((rc = dalloc(net, &net->desc, (size_t)net->nslot * net->N * net->desc_words * 4))) return rc;
+  if ((rc = dalloc(net, &net->vcol, (size_t)net->ncol * 4))) return rc;
+  if ((rc = dalloc(net, &net->colv, (size_t)net->ncol * 4))) return rc;
   if ((rc = dalloc(net, &net->cnt, (size_t)net->nslot * 4))) return rc;
   if ((rc = dalloc(net, &net->ccnt, (size_t)net->nslot * net->ncol * 4))) return rc;
   if ((rc = dalloc(net, &net->isum, (size_t)net->ncol * 4))) return rc;
@@ -365,6 +438,9 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if ((rc = dalloc(net, &net->rcnt, (size_t)net->update_grid * 8))) return rc;
   if ((rc = dalloc(net, &net->stage, (size_t)net->rec_region * net->update_grid * 8))) return rc;
   if ((rc = dalloc(net, &net->dhdr, 32))) return rc;
+  SNN_CUDA(net, cudaHostAlloc(&net->hstatus, 16, cudaHostAllocMapped));
+  SNN_CUDA(net, cudaHostGetDevicePointer(&net->hstatus_dev, net->hstatus, 0));
+  *net->hstatus = 0u;
   SNN_CUDA(net, cudaHostAlloc(&net->hhdr, 32, cudaHostAllocMapped));
   SNN_CUDA(net, cudaHostGetDevicePointer(&net->hhdr_dev, net->hhdr, 0));
   net->hmap_cap = std::min<long long>(net->rec_region * net->update_grid, kMappedRecords);
@@ -378,8 +454,14 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if ((rc = dalloc(net, &wtab, net->tables.wtab.size() * 4))) return rc;
   net->device_bytes -= net->tables.wtab.size() * 4;
 
+  std::vector<uint32_t> vcol, colv;
+  column_order(net->W, net->H, net->tile, &vcol, &colv);
   cudaError_t e = cudaMemcpyAsync(wtab, net->tables.wtab.data(), net->tables.wtab.size() * 4,
                                   cudaMemcpyHostToDevice, net->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(net->vcol, vcol.data(), vcol.size() * 4, cudaMemcpyHostToDevice, net->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(net->colv, colv.data(), colv.size() * 4, cudaMemcpyHostToDevice, net->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(net->ctl, 0, sizeof(Ctl), net->stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(net->cnt, 0, (size_t)net->nslot * 4, net->stream);
@@ -482,8 +564,9 @@ int snn_step(snn_net* net, int64_t n_steps) {
   if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
   if (net->in_batch) return fail(net, SNN_ESTATE, "net belongs to a batch: use snn_batch_step");
   if (n_steps < 0) return fail(net, SNN_EINVAL, "n_steps must be >= 0");
+  int rc = check_status(net);
+  if (rc) return rc;
   if (n_steps == 0) return SNN_OK;
-  int rc;
   if (n_steps >= net->graph_many_steps && !net->graph_many)
     if ((rc = capture(net, net->graph_many_steps, &net->graph_many))) return rc;
   if (!net->graph_one)
@@ -609,6 +692,7 @@ int snn_read_spikes(snn_net* net, int32_t* steps, int32_t* ids, int64_t cap, int
                                      net->dhdr, net->hhdr_dev, net->hmap_dev,
                                      net->hmap_dev + net->hmap_cap, net->hmap_cap, net->stream));
   SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+  if (int src = check_status(net)) return src;
   const long long kept = (long long)net->hhdr[0];
   bool lost = net->hhdr[1] != 0ull || kept > cap;
   const uint32_t tmin = (uint32_t)net->hhdr[2], tmax = (uint32_t)net->hhdr[3];
@@ -692,6 +776,7 @@ int snn_read_rates(snn_net* net, float* hz, int64_t n, float* pop_hz) {
   cudaError_t e;
   Ctl c = read_ctl(net, &e);
   if (e != cudaSuccess) return cuda_fail(net, e, "read control block");
+  if (int src = check_status(net)) return src;
   std::vector<unsigned long long> cnt((size_t)net->ncol * 2);
   SNN_CUDA(net, cudaMemcpyAsync(cnt.data(), net->colcnt, cnt.size() * 8, cudaMemcpyDeviceToHost,
                                 net->stream));
@@ -728,6 +813,7 @@ int snn_stats(snn_net* net, double* recurrent_events, double* external_events, i
   SNN_CUDA(net, cudaMemcpyAsync(syn.data(), net->syn_part, syn.size() * 8, cudaMemcpyDeviceToHost,
                                 net->stream));
   SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+  if (int src = check_status(net)) return src;
   unsigned long long se = 0ull, sy = 0ull;
   for (size_t b = 0; b < ext.size(); ++b) {
     se += ext[b];
@@ -785,7 +871,7 @@ int snn_read_synapses(snn_net* net, int64_t j0, int64_t n, int64_t* target, int3
         if (net->precision == SNN_EXACT_F16W) {
           uint32_t rec;
           std::memcpy(&rec, rp, 4);
-          if (rec == kPad) continue;
+          if (is_pad_f16(rec)) continue;
           code = rec & 0x1FFFFu;
           __half_raw hr;
           hr.x = (unsigned short)(rec >> 17);
@@ -832,10 +918,10 @@ int snn_row_lengths(snn_net* net, int64_t j0, int64_t n, int32_t* counts) {
 
 int snn_info(snn_net* net, int64_t* info, int n) {
   if (!net || !info) return fail(net, SNN_EINVAL, "null argument");
-  const int64_t v[6] = {net->N, (int64_t)net->total_syn, (int64_t)net->device_bytes,
+  const int64_t v[9] = {net->N, (int64_t)net->total_syn, (int64_t)net->device_bytes,
                         net->N * (int64_t)net->rowcap * net->rec_size, net->rowcap,
-                        net->precision};
-  for (int i = 0; i < n && i < 6; ++i) info[i] = v[i];
+                        net->precision, net->tile, net->deliver_grid, net->update_grid};
+  for (int i = 0; i < n && i < 9; ++i) info[i] = v[i];
   return SNN_OK;
 }
 
@@ -951,10 +1037,13 @@ int batch_run(snn_batch* b, long long n_steps) {
   bp.bar = b->d_bar;
   bp.spin_limit = b->spin_limit;
   bp.extra_arrivals = b->extra_arrivals;
-  const int grid = batch_grid(b->precision, b->infl, b->num_sms, b->max_npc);
+  size_t dsm = 0;
+  for (const snn_net* net : b->nets) dsm = std::max(dsm, deliver_smem(net->sp, b->precision));
+  const size_t smem = batch_smem(dsm);
+  const int grid = batch_grid(b->precision, b->infl, b->num_sms, smem);
   if (grid < 1) return bfail(b, SNN_ECUDA, "batch kernel does not fit on the device");
   SNN_BCUDA(b, cudaMemsetAsync(b->d_bar, 0, 3 * sizeof(unsigned), b->stream));
-  SNN_BCUDA(b, launch_batch(bp, b->precision, b->infl, grid, b->max_npc, b->stream));
+  SNN_BCUDA(b, launch_batch(bp, b->precision, b->infl, grid, smem, b->stream));
   unsigned flags[3] = {0u, 0u, 0u};
   SNN_BCUDA(b, cudaMemcpyAsync(flags, b->d_bar, sizeof(flags), cudaMemcpyDeviceToHost, b->stream));
   SNN_BCUDA(b, cudaStreamSynchronize(b->stream));

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
       const unsigned end = incl * kSlotUnit;
       for (unsigned s = s_cur[w][lane]; s < end; ++s) {
         if (PREC == SNN_EXACT_F16W)
-          static_cast<uint32_t*>(P.syn)[row + s] = kPad;
+          static_cast<uint32_t*>(P.syn)[row + s] = kPadF16;
         else
           static_cast<uint2*>(P.syn)[row + s] = make_uint2(kPad, 0u);
       }
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) paper_rows_kernel(const Buil
       const unsigned end = (unsigned)P.bend[j * kBendStride + lane] * kSlotUnit;
       for (unsigned s = s_cur[w][lane]; s < end; ++s) {
         if (PREC == SNN_EXACT_F16W)
-          static_cast<uint32_t*>(P.syn)[row + s] = kPad;
+          static_cast<uint32_t*>(P.syn)[row + s] = kPadF16;
         else
           static_cast<uint2*>(P.syn)[row + s] = make_uint2(kPad, 0u);
       }

@@ -8,6 +8,7 @@
 //          of 32 B sectors in the F16W layout).
 //            F16W: u32 record  = half_magnitude(15) << 17 | code(17)
 //            F32W: u32x2 record = { target neuron index, int32 round(w * 2^16) }
+//          padding records have weight 0 (kPadF16 / {kPad, 0}).
 //          (w the FP32 weight in mV, so the record holds exactly what is added)
 //          code = ((dy + 3) << 3 | (dx + 3)) << 11 | l  (stencil offset of the
 //          target column and index l inside it; local synapses use dx=dy=0).
@@ -17,15 +18,24 @@
 //   V, C   float[Npad] membrane potential (mV) and calcium.
 //   R      u8[Npad] remaining refractory steps.
 //   acc    int32[Npad] recurrent input of the next step, 2^-16 mV units.
-//   ids    u32[d_max + 1][N] spike lists of the last d_max + 1 steps (slot
-//          t % (d_max + 1)); the spikes of column c at step t are
-//          ids[slot][c * n_per_col + r], r < ccnt[slot][c], in no fixed order.
+//   desc   spike descriptors of the last d_max + 1 steps (slot t % (d_max +
+//          1)), desc_words u32 each: the spiker's id, then its bucket ends
+//          (bend[j][0 .. ndel - 1], one byte each).  The spikes of column c
+//          at step t are entries [slot][c * n_per_col + r], r < ccnt[slot][c],
+//          in no fixed order.
 //   ccnt   u32[d_max + 1][ncol] spikes of each slot's step per column.
-//   isum   u32[ncol] (bucket, spiker) items of each column over the steps that
-//          the next delivery reads (the sum of its d_max - d_min + 1 slots).
-//   gsum   u32[ceil(ncol / 32)] isum summed over groups of 32 columns.
+//   vcol, colv  u32[ncol] delivery order of the columns: virtual column v is
+//          real column vcol[v]; colv is the inverse.  Columns are numbered
+//          tile by tile (tiles of `tile` x `tile` columns in row-major order,
+//          row-major inside a tile), so a run of virtual columns is a compact
+//          patch of the grid.
+//   isum   u32[ncol] (bucket, spiker) items of each virtual column over the
+//          steps that the next delivery reads (the sum of its d_max - d_min +
+//          1 slots).
+//   gsum   u32[ceil(ncol / 32)] isum summed over groups of 32 virtual columns.
 //   cnt    u32[d_max + 1] spikes of each slot's step.
-//   ctl    control block (step counter, completion counter, overflow flag).
+//   ctl    control block (step counter, completion counter, overflow flag,
+//          status).
 //   rec    u64 spike records (step << 32 | id), one region per update block,
 //          rcnt[b] records in region b since the last drain.
 //   colcnt u64[ncol][2] spike counts per column and population.
@@ -53,9 +63,15 @@ constexpr int kBendStride = 32;  // bytes of bucket ends per neuron
 constexpr int kSlotUnit = 8;     // buckets are padded to 8 synapse slots
 constexpr int kMaxPoisThr = 127; // Poisson thresholds below 2^32
 constexpr int kMaxOff = 48;      // remote stencil offsets (radius <= 3)
-constexpr uint32_t kPad = 0xFFFFFFFFu;  // code of a padding record
+constexpr uint32_t kPad = 0xFFFFFFFFu;  // target of an F32W padding record (weight 0)
+// F16W padding record: weight magnitude 0 and stencil field dx + 3 = 7, which
+// no synapse uses (|dx| <= 3).
+constexpr uint32_t kPadF16 = 7u << 11;
+__host__ __device__ constexpr bool is_pad_f16(uint32_t rec) { return ((rec >> 11) & 7u) == 7u; }
 constexpr int kCenterCode = (3 << 3) | 3;
 constexpr int kMaxGridSide = 16383;     // columns per grid side (14-bit coordinates)
+constexpr int kMaxTile = 8;             // delivery tile side, columns
+constexpr int kMaxTileCols = kMaxTile * kMaxTile;
 
 // Tables computed on the host in FP64 and rounded once.
 struct HostTables {
@@ -91,15 +107,22 @@ struct Ctl {
   unsigned int drained;         // blocks done with the current record drain
   unsigned int done;            // delivery blocks finished this step
   unsigned int rec_overflow;    // set when a record did not fit its region
-  unsigned int pad;
+  unsigned int status;          // nonzero: a delivery found inconsistent counts
 };
+
+// Status codes a kernel leaves in Ctl::status (and the mapped host word).
+constexpr unsigned kStatusCounts = 1u;  // item counts disagree with the spike lists
 
 // Everything a step kernel needs, passed by value (constant bank).
 struct StepParams {
   long long N;
   int npc, nexc, W, H, K, dmin, ndel, nslot, rowcap;
   int ncol;
-  int agg;  // block shared windows for the local half of the synapses
+  int agg;  // shared-memory windows over each delivery tile and its ring
+  int tile, ring;          // delivery tile side and window ring, in columns
+  int win_cap;             // ints of the window (largest tile window)
+  int desc_words;          // u32 words per spike descriptor (8 or 16)
+  uint32_t npc_m, w_m;     // floor(2^32 / n_per_col), floor(2^32 / W) (capped)
   uint32_t seed_lo, seed_hi;
   float theta, vr, dc, pvv, pcc, pvc_e, pvc_i;
   int32_t jx;
@@ -111,7 +134,11 @@ struct StepParams {
   float* C;
   uint8_t* R;
   int32_t* acc;
-  uint32_t* ids;
+  uint32_t* ids;   // compact spike-id list (no descriptors: noalloc form only)
+  uint32_t* desc;  // spike descriptors (see above); null: write ids instead
+  const uint32_t* vcol;
+  const uint32_t* colv;
+  unsigned* hstatus;  // mapped host copy of Ctl::status (may be null)
   unsigned* cnt;
   unsigned* ccnt;  // per-column counts (column-indexed lists); null: one compact list
   unsigned* isum;  // per-column items of the delivery window (with ccnt)
@@ -188,8 +215,12 @@ cudaError_t launch_paper_fill(const BuildParams& bp, int precision, int num_sms,
 cudaError_t launch_init_state(const StepParams& p, cudaStream_t st);
 cudaError_t launch_update(const StepParams& p, int grid, cudaStream_t st);
 int update_grid(long long N, int num_sms);
+// Delivery: dynamic shared memory of one block (table, F16W neighbour table,
+// window), its thread count, and the persistent grid (0 if it does not fit).
+size_t deliver_smem(const StepParams& p, int precision);
+int deliver_threads();
+int deliver_grid(const StepParams& p, int precision, int num_sms);
 cudaError_t launch_deliver(const StepParams& p, int precision, int grid, cudaStream_t st);
-int deliver_grid(int precision, int num_sms, int npc, bool agg);
 // Compact the per-block record regions into id and step arrays and reset
 // them; header = {records kept, 1 if records were dropped, first step, last
 // step}, written to header and to the mapped host header map_hdr.  The arrays
@@ -200,9 +231,11 @@ cudaError_t launch_drain_records(const StepParams& p, int nreg, uint32_t* stage_
                                  uint32_t* stage_steps, unsigned long long* header,
                                  unsigned long long* map_hdr, uint32_t* map_ids,
                                  uint32_t* map_steps, long long map_cap, cudaStream_t st);
-size_t batch_smem(int max_npc);
-int batch_grid(int precision, int infl, int num_sms, int max_npc);
-cudaError_t launch_batch(const BatchParams& b, int precision, int infl, int grid, int max_npc,
+// Batch kernel: dynamic shared memory for members whose largest delivery
+// layout is max_deliver_smem, its grid (0 if it does not fit), its launch.
+size_t batch_smem(size_t max_deliver_smem);
+int batch_grid(int precision, int infl, int num_sms, size_t smem);
+cudaError_t launch_batch(const BatchParams& b, int precision, int infl, int grid, size_t smem,
                          cudaStream_t st);
 cudaError_t launch_sum_parts(const unsigned long long* part, int n, unsigned long long* out,
                              cudaStream_t st);

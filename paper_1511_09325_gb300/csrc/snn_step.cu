@@ -7,27 +7,32 @@
 //   recurrent input, applies refractoriness, threshold, reset and the exact
 //   propagator with explicitly rounded FP32 operations.  A tile's spikes are
 //   counted per column in shared memory and written to their column's part of
-//   the step's spike list (one atomic per column and tile) and to the block's
-//   record region.  The per-column item counts of the next delivery (isum,
-//   gsum) are kept up to date here; spike and external-event totals go to
-//   per-block partial sums.
+//   the step's spike list (one atomic per column and tile) as descriptors --
+//   the spiker's id and its bucket ends, so that a delivery finds a bucket
+//   with one load -- and to the block's record region.  The per-column item
+//   counts of the next delivery (isum, gsum) are kept up to date here; spike
+//   and external-event totals go to per-block partial sums.
 //
 // deliver_kernel (event-driven delivery, Sec. 1), "pull by delay": the input
 //   of step t+1 is the sum over delays d of bucket d of every neuron that
 //   spiked at step t+1-d, so only one N-entry accumulator (resident in L2)
 //   receives additions, not a d_max-slot ring.  The (delay bucket, spiker)
-//   items of the last d_max steps, ordered by (column, bucket, spiker), form
-//   one virtual list split evenly over a persistent grid.  A warp takes 32
-//   consecutive items: lane e resolves item e, then the warp streams the
-//   concatenated buckets in 16-byte chunks (4 synapses per lane, four chunks in
-//   flight).  The item a chunk belongs to is found from a ballot over the
-//   items' start offsets and the item's fields travel by shuffle, so the inner
-//   loop reads no shared memory.  Each synapse's weight goes to L2 as a
-//   fire-and-forget int32 reduction, except that synapses onto the first
-//   columns of a block's range (where its spikers sit, so about half of their
-//   synapses) are summed in shared-memory windows and flushed once per block.
-//   Integer addition makes the result independent of the order.  The last
-//   block to finish advances the step counter.
+//   items of the last d_max steps, ordered by (virtual column, bucket,
+//   spiker), form one virtual list split evenly over a persistent grid of one
+//   1024-thread block per SM.  Virtual columns run tile by tile (tiles of
+//   tile x tile columns), so a block's items come from a compact patch of the
+//   grid.  For each tile part with enough items, a block keeps a
+//   shared-memory window over the tile's columns and a ring of one column
+//   around them -- where about seven eighths of the tile's synapses land (the
+//   local half and most of the near stencil) -- sums those synapses there
+//   with shared-memory reductions and flushes the window once into the
+//   accumulator; the other synapses go to L2 as fire-and-forget int32
+//   reductions.  A warp takes batches of 32 items: lane e resolves item e (a
+//   binary search in the tile part's table of (column, bucket) counts and one
+//   descriptor load) and streams that bucket by itself, 32-byte sectors
+//   double-buffered in registers; the next batch is resolved before the
+//   current one is streamed.  Integer addition makes the result independent
+//   of the order.  The last block to finish advances the step counter.
 #include "snn_device.cuh"
 #include "snn_internal.h"
 
@@ -35,12 +40,16 @@ namespace snn {
 namespace {
 
 constexpr int kUpdateThreads = 256;
-constexpr int kDeliverThreads = 256;
-constexpr int kBatchThreads = kUpdateThreads;  // the batch kernel runs both bodies
-constexpr int kInflight = 4;     // 16-byte synapse chunks in flight per lane (F32W: 2 loads each)
-constexpr int kInflightF16 = 4;  // the same for F16W (one load each)
+constexpr int kDeliverThreads = 1024;  // one delivery block per SM
+constexpr int kBatchThreads = 1024;    // batch kernel: 4 update sub-blocks or one delivery block
+constexpr int kUpdateSubs = kBatchThreads / kUpdateThreads;
+constexpr int kInflightF32 = 1;  // 32-byte sectors per lane and stage, F32W (2 loads each)
+constexpr int kInflightF16 = 2;  // the same for F16W (two stages in flight)
 constexpr int kTile = kUpdateThreads * 4;    // neurons per update tile
 constexpr int kTileCols = kTile / 2 + 2;     // columns a tile can touch (npc >= 2)
+constexpr int kBatchItems = 32;              // items per warp batch (one per lane)
+constexpr unsigned kMinItems = 256;          // fewest items a delivery block takes
+constexpr unsigned kWinMinItems = 1024;      // fewest items of a tile part that uses the window
 
 struct NeuronOut {
   float v, c;
@@ -105,6 +114,23 @@ __device__ __forceinline__ void red_add_if(uint32_t on, int32_t* p, int32_t v, u
       : "memory");
 }
 
+// The two predicated reductions of the record path, without a compiler
+// memory barrier: nothing the delivery loop reads aliases the window or the
+// accumulator (both are read only after the block's next barrier), so the
+// compiler may move loads of the synapse table across them.
+__device__ __forceinline__ void red_add_if_nb(uint32_t on, int32_t* p, int32_t v, uint64_t pol) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+      "@q red.global.add.L2::cache_hint.s32 [%1], %2, %3;\n\t}" ::"r"(on),
+      "l"(p), "r"(v), "l"(pol));
+}
+__device__ __forceinline__ void red_shared_if_nb(uint32_t on, uint32_t a, int32_t v) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+      "@q red.shared.add.s32 [%1], %2;\n\t}" ::"r"(on),
+      "r"(a), "r"(v));
+}
+
 // Predicated int32 reduction into shared memory (shared-window address `a`).
 __device__ __forceinline__ void red_shared_if(uint32_t on, uint32_t a, int32_t v) {
   asm volatile(
@@ -114,7 +140,46 @@ __device__ __forceinline__ void red_shared_if(uint32_t on, uint32_t a, int32_t v
       : "memory");
 }
 
-// Shared memory of one update block.
+// Loads of the neuron state, read once per step: no L1 allocation, so that
+// L1 capacity does not bound the loads a block keeps in flight.
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int4 ld_stream(const int4* p) {
+  int4 v;
+  asm volatile("ld.global.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uchar4 ld_stream(const uchar4* p) {
+  uint32_t v;
+  asm volatile("ld.global.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return make_uchar4((unsigned char)v, (unsigned char)(v >> 8), (unsigned char)(v >> 16),
+                     (unsigned char)(v >> 24));
+}
+
+// Barrier of an update body: the whole block (bar 0) or one 256-thread
+// sub-block of the batch kernel (named barrier `bar`).
+__device__ __forceinline__ void body_sync(int bar) {
+  if (bar == 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(kUpdateThreads) : "memory");
+}
+
+// Records the first inconsistency a kernel finds; the host turns it into
+// SNN_ESTATE.
+__device__ __forceinline__ void set_status(const StepParams& P, unsigned code) {
+  atomicOr(&P.ctl->status, code);
+  if (P.hstatus != nullptr) *reinterpret_cast<volatile unsigned*>(P.hstatus) = code;
+}
+
+// Shared memory of one update body.
 struct UpdateSmem {
   uint32_t thr[kMaxPoisThr + 1];  // Poisson thresholds
   uint8_t guide[256];            // Poisson guide table
@@ -128,18 +193,20 @@ struct UpdateSmem {
   unsigned ksum[kUpdateThreads / 32];
 };
 
-// Update block vb of vgrid for step t: tiles vb, vb + vgrid, ...  Block vb
-// owns ext_part[vb], spk_part[vb] and record region vb of the net, so the
-// grid size must be the same every step.  Each spike goes to the step's list
-// (column c's part when P.ccnt is set, else one compact list) and to the
-// block's record region as (step << 32 | id).
+// Update body vb of vgrid for step t, run by kUpdateThreads threads (thread
+// index tid, barrier `bar`): tiles vb, vb + vgrid, ...  Body vb owns
+// ext_part[vb], spk_part[vb] and record region vb of the net, so the grid
+// size must be the same every step.  Each spike goes to the step's list
+// (column c's part when P.ccnt is set, else one compact list) -- as a
+// descriptor when P.desc is set, else as its id -- and to the body's record
+// region as (step << 32 | id).
 __device__ __forceinline__ void update_body(const StepParams& P, long long t, int vb, int vgrid,
-                                            UpdateSmem& S) {
-  __syncthreads();  // the shared memory may still be read by a previous body
+                                            UpdateSmem& S, int tid, int bar) {
+  body_sync(bar);  // the shared memory may still be read by a previous body
   const int slot = (int)(t % P.nslot);
-  for (int m = threadIdx.x; m < 256; m += blockDim.x) S.guide[m] = P.pois_guide[m];
-  for (int m = threadIdx.x; m <= kMaxPoisThr; m += blockDim.x) S.thr[m] = P.pois_thr[m];
-  if (threadIdx.x == 0) {
+  for (int m = tid; m < 256; m += kUpdateThreads) S.guide[m] = P.pois_guide[m];
+  for (int m = tid; m <= kMaxPoisThr; m += kUpdateThreads) S.thr[m] = P.pois_thr[m];
+  if (tid == 0) {
     S.rc = P.rcnt[vb];
     S.spk = 0ull;
   }
@@ -166,22 +233,22 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
     // neuron indices are below 2^31: 32-bit divisions are exact (and cheap)
     const int col0 = (int)((uint32_t)first / (uint32_t)P.npc);
     const int ncols = (int)((uint32_t)last / (uint32_t)P.npc) - col0 + 1;
-    for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
+    for (int k = tid; k < ncols; k += kUpdateThreads) {
       S.tpop[k][0] = 0u;
       S.tpop[k][1] = 0u;
     }
-    __syncthreads();
+    body_sync(bar);
 
-    const long long q = tile * kUpdateThreads + threadIdx.x;
+    const long long q = tile * kUpdateThreads + tid;
     const long long i0 = q * 4;
     unsigned rank[4] = {0u, 0u, 0u, 0u};
     int scol[4] = {-1, -1, -1, -1};
     if (i0 < P.N) {
       const uint4 x = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)t, kTagExt, 0u), P.seed_lo, P.seed_hi);
-      const float4 v4 = reinterpret_cast<const float4*>(P.V)[q];
-      const float4 c4 = reinterpret_cast<const float4*>(P.C)[q];
-      const uchar4 r4 = reinterpret_cast<const uchar4*>(P.R)[q];
-      const int4 a4 = reinterpret_cast<const int4*>(P.acc)[q];
+      const float4 v4 = ld_stream(reinterpret_cast<const float4*>(P.V) + q);
+      const float4 c4 = ld_stream(reinterpret_cast<const float4*>(P.C) + q);
+      const uchar4 r4 = ld_stream(reinterpret_cast<const uchar4*>(P.R) + q);
+      const int4 a4 = ld_stream(reinterpret_cast<const int4*>(P.acc) + q);
       reinterpret_cast<int4*>(P.acc)[q] = make_int4(0, 0, 0, 0);
       const float vin[4] = {v4.x, v4.y, v4.z, v4.w};
       const float cin[4] = {c4.x, c4.y, c4.z, c4.w};
@@ -219,11 +286,11 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
       reinterpret_cast<uchar4*>(P.R)[q] = make_uchar4((unsigned char)rout[0], (unsigned char)rout[1],
                                                       (unsigned char)rout[2], (unsigned char)rout[3]);
     }
-    __syncthreads();
-    // places: records grouped by column (E then I) in the block's region; list
+    body_sync(bar);
+    // places: records grouped by column (E then I) in the body's region; list
     // entries in each column's part of the step's list (or the compact list)
     if (P.ccnt != nullptr) {
-      for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
+      for (int k = tid; k < ncols; k += kUpdateThreads) {
         const unsigned n = S.tpop[k][0] + S.tpop[k][1];
         const int c = col0 + k;
         S.lbase[k] = (long long)c * P.npc +
@@ -231,12 +298,13 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
         unsigned d = P.dmin == 1 ? n : 0u;
         if ((long long)c * P.npc >= first) d += (cin_ ? cin_[c] : 0u) - cout_[c];
         if (d) {
-          atomicAdd(P.isum + c, d);
-          atomicAdd(P.gsum + (c >> 5), d);
+          const int v = P.colv != nullptr ? (int)P.colv[c] : c;
+          atomicAdd(P.isum + v, d);
+          atomicAdd(P.gsum + (v >> 5), d);
         }
       }
     }
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       unsigned pos = 0u;
       for (int k = 0; k < ncols; ++k) {
         S.tpos[k] = pos;
@@ -247,7 +315,7 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
       S.rc += pos;
       S.spk += pos;
     }
-    __syncthreads();
+    body_sync(bar);
     const unsigned long long rc = S.rbase;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -256,31 +324,42 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
         const unsigned r = rank[e] & 0x7FFFFFFFu;
         const unsigned off = (rank[e] & 0x80000000u) ? S.tpop[k][0] + r : r;
         const uint32_t id = (uint32_t)(i0 + e);
-        list[P.ccnt != nullptr ? S.lbase[k] + off : S.cbase + S.tpos[k] + off] = id;
+        const long long pos = P.ccnt != nullptr ? S.lbase[k] + off : S.cbase + S.tpos[k] + off;
+        if (P.desc != nullptr) {
+          // descriptor: id, then the bucket ends of the spiker's row
+          uint4* d = reinterpret_cast<uint4*>(P.desc + ((long long)slot * P.N + pos) * P.desc_words);
+          const uint4* be = reinterpret_cast<const uint4*>(P.bend + (long long)id * kBendStride);
+          const uint4 a = be[0], b = be[1];
+          d[0] = make_uint4(id, a.x, a.y, a.z);
+          d[1] = make_uint4(a.w, b.x, b.y, b.z);
+          if (P.desc_words == 16) d[2] = make_uint4(b.w, 0u, 0u, 0u);
+        } else {
+          list[pos] = id;
+        }
         syn += P.deg != nullptr ? P.deg[id] : (uint32_t)P.K;
         const unsigned long long ri = rc + S.tpos[k] + off;
         if ((long long)ri < P.rec_region) region[ri] = ((unsigned long long)(unsigned)t << 32) | id;
       }
     }
-    for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
+    for (int k = tid; k < ncols; k += kUpdateThreads) {
       if (S.tpop[k][0]) atomicAdd(&P.colcnt[2 * (col0 + k)], (unsigned long long)S.tpop[k][0]);
       if (S.tpop[k][1]) atomicAdd(&P.colcnt[2 * (col0 + k) + 1], (unsigned long long)S.tpop[k][1]);
     }
-    __syncthreads();
+    body_sync(bar);
   }
 
-  // external and synaptic events: per-block partial sums, no atomics
+  // external and synaptic events: per-body partial sums, no atomics
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     ksum += __shfl_xor_sync(0xFFFFFFFFu, ksum, o);
     syn += __shfl_xor_sync(0xFFFFFFFFu, syn, o);
   }
-  if ((threadIdx.x & 31) == 0) {
-    S.ksum[threadIdx.x >> 5] = ksum;
-    S.synw[threadIdx.x >> 5] = syn;
+  if ((tid & 31) == 0) {
+    S.ksum[tid >> 5] = ksum;
+    S.synw[tid >> 5] = syn;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  body_sync(bar);
+  if (tid == 0) {
     unsigned long long tot = 0ull, tsyn = 0ull;
     for (int w = 0; w < kUpdateThreads / 32; ++w) {
       tot += S.ksum[w];
@@ -296,75 +375,83 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
 
 __global__ void __launch_bounds__(kUpdateThreads, 5) update_kernel(const StepParams P) {
   __shared__ UpdateSmem S;
-  update_body(P, P.ctl->t, (int)blockIdx.x, (int)gridDim.x, S);
+  update_body(P, P.ctl->t, (int)blockIdx.x, (int)gridDim.x, S, (int)threadIdx.x, 0);
 }
 
-// Periodic coordinate v in [-3, n + 3); one conditional correction suffices
-// when the period is at least 4.
-__device__ __forceinline__ int wrap_near(int v, int n) {
-  if (n >= 4) {
-    v += (v < 0) ? n : 0;
-    v -= (v >= n) ? n : 0;
-    return v;
-  }
-  return wrap(v, n);
+// ---------------------------------------------------------------------------
+// Delivery.
+// ---------------------------------------------------------------------------
+
+// Quotient of x by d from m = min(floor(2^32 / d), 2^32 - 1): the estimate
+// is at most one below the quotient, so one correction step finishes it.
+__device__ __forceinline__ uint32_t div_by(uint32_t x, uint32_t d, uint32_t m) {
+  uint32_t q = __umulhi(x, m);
+  if (x - q * d >= d) ++q;
+  return q;
 }
 
-constexpr int kWindows = 4;        // shared-memory windows (columns) per delivery block
-constexpr int kBatchItems = 16;    // items per warp batch (at most 32)
-// (column, bucket) entries per table piece, at most: 4 per thread
-constexpr int kTabEntries = 4 * (kDeliverThreads > kBatchThreads ? kDeliverThreads : kBatchThreads);
-// A piece spans at most kPieceCols columns; for F16W each has 64 entries
-// (one per stencil code) in the neighbour table.
-constexpr int kPieceCols = 32;
-constexpr int kNbEntries = 64 * kPieceCols;
+// Tile of virtual column v: tiles of P.tile x P.tile columns in row-major
+// order (those of the last tile row or column may be smaller), columns
+// row-major inside a tile.
+struct TileGeo {
+  int first;   // virtual index of the tile's first column
+  int x0, y0;  // grid position of its first column
+  int tw, th;  // its width and height
+};
 
-// Per-item info travelling with a chunk: the spiker's column cx | cy << 14
-// and whether it is inhibitory (bit 28).
-__device__ __forceinline__ uint32_t pack_info(int cx, int cy, bool inh) {
-  return (uint32_t)cx | ((uint32_t)cy << 14) | ((inh ? 1u : 0u) << 28);
+__device__ __forceinline__ TileGeo tile_geo(const StepParams& P, int v) {
+  TileGeo g;
+  const int rowcols = P.tile * P.W;  // columns of a full row of tiles
+  const int tr = v / rowcols;
+  g.y0 = tr * P.tile;
+  g.th = min(P.tile, P.H - g.y0);
+  const int rem = v - tr * rowcols;
+  const int tc = rem / (g.th * P.tile);
+  g.x0 = tc * P.tile;
+  g.tw = min(P.tile, P.W - g.x0);
+  g.first = tr * rowcols + tc * g.th * P.tile;
+  return g;
 }
 
-// Deliver one synapse record of a spiker whose column info is `info`.
-// Targets in neurons wbase .. wbase + wlen - 1 (the block's window columns)
-// are summed in the shared windows at shared address win_s, the others
-// reduced into L2.  Padding records deliver nothing.  Both reductions are
-// predicated, so the warp never diverges here.
-template <int PREC>
-__device__ __forceinline__ void deliver_record(uint32_t code, uint32_t wbits, uint32_t info,
-                                               uint32_t win_s, uint32_t wbase, uint32_t wlen,
-                                               uint64_t pol, const uint32_t* nb,
-                                               const StepParams& P) {
-  const bool valid = code != kPad;
-  uint32_t target;
-  int32_t wfx;
-  if (PREC == SNN_EXACT_F16W) {
-    const float wscale = (info >> 28) & 1u ? -65536.0f : 65536.0f;
-    wfx = __float2int_rn(__fmul_rn(__half2float(__ushort_as_half((unsigned short)wbits)), wscale));
-    // first neuron of the target column, from the piece's neighbour table
-    const uint32_t off = (code >> 11) & 63u;
-    target = nb[(info & 0x3Fu) * 64u + (valid ? off : 0u)] + (code & 0x7FFu);
-  } else {
-    wfx = (int32_t)wbits;
-    target = code;
-  }
-  const uint32_t rel = target - wbase;
-  const bool inwin = rel < wlen;
-  red_shared_if(valid && inwin, win_s + 4u * rel, wfx);
-  red_add_if(valid && !inwin, P.acc + (valid ? target : 0u), wfx, pol);
+// Shared-memory window of a tile: the ww x wh columns starting at (x0, y0)
+// (periodic; at most the whole grid, so every column appears once).  Slot
+// (rx, ry) holds column ((x0 + rx) mod W, (y0 + ry) mod H).
+struct WinGeo {
+  int x0, y0, ww, wh;
+};
+
+__device__ __forceinline__ WinGeo win_geo(const StepParams& P, const TileGeo& g, bool on) {
+  WinGeo w;
+  w.ww = min(g.tw + 2 * P.ring, P.W);
+  w.wh = min(g.th + 2 * P.ring, P.H);
+  w.x0 = w.ww == P.W ? 0 : wrap(g.x0 - P.ring, P.W);
+  w.y0 = w.wh == P.H ? 0 : wrap(g.y0 - P.ring, P.H);
+  if (!on) w.ww = w.wh = 0;
+  return w;
 }
 
 struct DeliverSmem {
-  unsigned tab[kTabEntries + 1];  // items before each (column, bucket) entry of the piece
-  int slot[kMaxDelays];           // slot of each bucket's step, -1 before step 0
   unsigned long long wsum[32];    // per-warp sums of block_scan
   unsigned long long xgp[2];      // items before the group holding lo / hi - 1
-  unsigned long long p0;          // items before column c0
+  unsigned long long p0;          // items before virtual column v0
   int xg[2];                      // group holding lo / hi - 1
-  int c0, c1;                     // first and last column of the block's items
-  unsigned next;                  // next batch of the current piece
+  int v0, v1;                     // first and last virtual column of the block's items
+  int slot[kMaxDelays];           // slot of each bucket's step, -1 before step 0
+  int ccol[kMaxTileCols];         // real column of each column of the current tile part
+  int cx[kMaxTileCols], cy[kMaxTileCols];  // its grid position
+  uint32_t wbase[(kMaxTile + 2) * (kMaxTile + 2)];  // first neuron of each window slot's column
+  unsigned next;                  // next batch of the current tile part
 };
-constexpr size_t kDeliverSmemPad = (sizeof(DeliverSmem) + 255) / 256 * 256;
+
+// Words of the (column, bucket) table and of the F16W neighbour table in the
+// dynamic shared memory of a delivery block; the window follows them.
+__device__ __forceinline__ int tab_words(const StepParams& P) {
+  return (P.tile * P.tile * P.ndel + 1 + 3) & ~3;
+}
+template <int PREC>
+__device__ __forceinline__ int nb_words(const StepParams& P) {
+  return PREC == SNN_EXACT_F16W ? P.tile * P.tile * 64 : 0;
+}
 
 // Block-wide exclusive scan of one 64-bit value per thread; *total gets the
 // sum.  Uses S.wsum; contains two barriers.
@@ -391,169 +478,218 @@ __device__ __forceinline__ unsigned long long block_scan(unsigned long long v, D
   return before + incl - v;
 }
 
-// One warp, one batch of up to 32 items [item, hi) of a table piece whose
-// first column is pc: item k lies in entry e (column pc + e / ndel, bucket
-// e % ndel) with tab[e] <= k < tab[e + 1].
-template <int PREC, int INFL>
-__device__ __forceinline__ void deliver_batch(const StepParams& P, unsigned item, unsigned hi,
-                                              const DeliverSmem& S, int n_entries, int pc,
-                                              uint32_t win_s, uint32_t wbase, uint32_t wlen,
-                                              uint64_t pol, const uint32_t* nb) {
-  const int lane = threadIdx.x & 31;
-  int len = 0;
-  unsigned long long base = 0ull;
-  uint32_t info = 0u;
+// rint(x) for |x| < 2^22 by one rounded addition: x + 1.5 * 2^23 lands in
+// [2^23, 2^24), where the float grid is the integers, so the addition rounds
+// x to the nearest integer (ties to even) and the low mantissa bits hold it.
+constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr int32_t kRoundMagicBits = 0x4B400000;
+
+// Deliver one synapse of weight wfx (2^-16 mV units) to the shared-window
+// address `sa` (inwin) or to the accumulator at byte offset `gofs`; zero
+// weights (padding records, unused slots) deliver nothing.  Both reductions
+// are predicated, so the warp never diverges here.
+__device__ __forceinline__ void deliver_to(int32_t wfx, bool inwin, uint32_t sa, uint32_t gofs,
+                                           const StepParams& P, uint64_t pol) {
+  const uint32_t on = wfx != 0 ? 1u : 0u;
+  red_shared_if_nb(on & (inwin ? 1u : 0u), sa, wfx);
+  red_add_if_nb(on & (inwin ? 0u : 1u),
+                reinterpret_cast<int32_t*>(reinterpret_cast<char*>(P.acc) + gofs), wfx, pol);
+}
+
+// F16W record w = half_magnitude(15) << 17 | offset(6) << 11 | l(11): the
+// offset picks, in the neighbour-table row `nbrow` of the spiker's column, the
+// target column -- its shared window address, or bit 31 set and its first
+// neuron in the accumulator.
+__device__ __forceinline__ void deliver_f16(uint32_t w, uint32_t nbrow, float wsign,
+                                            const StepParams& P, uint64_t pol) {
+  uint32_t e;
+  asm("ld.shared.u32 %0, [%1];" : "=r"(e) : "r"(nbrow + ((w >> 9) & 0xFCu)));
+  const uint32_t l4 = (w << 2) & 0x1FFCu;
+  const float hf = __half2float(__ushort_as_half((unsigned short)(w >> 17)));
+  const int32_t wfx = __float_as_int(__fmaf_rn(hf, wsign, kRoundMagic)) - kRoundMagicBits;
+  deliver_to(wfx, (int)e >= 0, e + l4, (e << 2) + l4, P, pol);
+}
+
+// F32W record {target neuron, round(w * 2^16)}: the target's column is tested
+// against the tile's window.
+__device__ __forceinline__ void deliver_f32(uint32_t t, int32_t wfx, const WinGeo& wg,
+                                            uint32_t win_s, const StepParams& P, uint64_t pol) {
+  const uint32_t col = div_by(t, (uint32_t)P.npc, P.npc_m);
+  const uint32_t l = t - col * (uint32_t)P.npc;
+  const uint32_t y = div_by(col, (uint32_t)P.W, P.w_m);
+  const uint32_t x = col - y * (uint32_t)P.W;
+  int rx = (int)x - wg.x0;
+  rx += rx < 0 ? P.W : 0;
+  int ry = (int)y - wg.y0;
+  ry += ry < 0 ? P.H : 0;
+  const bool inwin = (unsigned)rx < (unsigned)wg.ww && (unsigned)ry < (unsigned)wg.wh;
+  const uint32_t wt = ((uint32_t)ry * (uint32_t)wg.ww + (uint32_t)rx) * (uint32_t)P.npc + l;
+  deliver_to(wfx, inwin, win_s + 4u * wt, t << 2, P, pol);
+}
+
+// A resolved item: the bucket a lane streams.
+struct Item {
+  const uint4* src;  // first 16 bytes of the bucket
+  int units;         // 32-byte sectors
+  uint32_t nbrow;    // F16W: shared address of the neighbour-table row of its column
+  float wsign;       // F16W: +-2^16, the sign of the spiker's population
+};
+
+// Lane's item `item` of a tile part whose (column, bucket) table is
+// tab[0 .. n_entries] (none when item >= hi): item k lies in entry e (column
+// S.ccol[e / ndel], bucket e % ndel) with tab[e] <= k < tab[e + 1].  Its
+// descriptor is read here; the bucket itself is streamed by stream_items.
+template <int PREC>
+__device__ __forceinline__ Item resolve_item(const StepParams& P, unsigned item, unsigned hi,
+                                             const DeliverSmem& S, const unsigned* tab,
+                                             int n_entries, uint32_t nb_s) {
+  Item it;
+  it.src = nullptr;
+  it.units = 0;
+  it.nbrow = 0u;
+  it.wsign = 65536.0f;
   if (item < hi) {
     int lo_e = 0, hi_e = n_entries;  // tab[lo_e] <= item < tab[hi_e]
     while (hi_e - lo_e > 1) {
       const int mid = (lo_e + hi_e) >> 1;
-      if (S.tab[mid] <= item)
+      if (tab[mid] <= item)
         lo_e = mid;
       else
         hi_e = mid;
     }
     const int k = lo_e / P.ndel;
     const int b = lo_e - k * P.ndel;
-    const int c = pc + k;
-    const uint32_t j = P.ids[(long long)S.slot[b] * P.N + (long long)c * P.npc + (item - S.tab[lo_e])];
-    const uint8_t* be = P.bend + (long long)j * kBendStride;
-    const int beg = (b ? (int)be[b - 1] : 0) * kSlotUnit;
-    const int end = (int)be[b] * kSlotUnit;
-    len = end - beg;
-    base = (unsigned long long)j * (unsigned long long)P.rowcap + (unsigned long long)beg;
-    const bool inh = (int)(j - (uint32_t)c * (uint32_t)P.npc) >= P.nexc;
-    if (PREC == SNN_EXACT_F16W) {
-      info = (uint32_t)k | ((inh ? 1u : 0u) << 28);  // column within the piece
-    } else {
-      const int cy = c / P.W;
-      info = pack_info(c - cy * P.W, cy, inh);
-    }
+    const int c = S.ccol[k];
+    const uint32_t* D =
+        P.desc + ((unsigned long long)S.slot[b] * (unsigned long long)P.N +
+                  (unsigned long long)c * (unsigned long long)P.npc + (item - tab[lo_e])) *
+                     (unsigned long long)P.desc_words;
+    // the descriptor: word 0 the spiker, bytes 4.. its bucket ends (units of
+    // 8 slots); bucket b spans ends[b - 1] .. ends[b] (bytes 3 + b and 4 + b)
+    const uint32_t j = D[0];
+    const int w = (3 + b) >> 2, sh = (3 + b) & 3;
+    const uint32_t lo_w = w == 0 ? j : D[w];
+    const uint32_t hi_w = sh == 3 ? D[w + 1] : 0u;
+    const uint32_t ends = __funnelshift_r(lo_w, hi_w, 8 * sh);
+    const int beg = b ? (int)(ends & 0xFFu) : 0;
+    const int end = (int)((ends >> 8) & 0xFFu);
+    // an 8-slot unit is one sector (F16W) or two (F32W)
+    it.units = (end - beg) * (PREC == SNN_EXACT_F16W ? 1 : 2);
+    const unsigned long long slot0 =
+        (unsigned long long)j * (unsigned long long)P.rowcap + (unsigned long long)beg * kSlotUnit;
+    it.src = reinterpret_cast<const uint4*>(static_cast<const char*>(P.syn) +
+                                            slot0 * (PREC == SNN_EXACT_F16W ? 4ull : 8ull));
+    it.nbrow = nb_s + (uint32_t)k * 256u;
+    it.wsign = (int)(j - (uint32_t)c * (uint32_t)P.npc) >= P.nexc ? -65536.0f : 65536.0f;
   }
-  // compact the non-empty items to lanes 0..nit-1
-  const unsigned cm = __ballot_sync(0xFFFFFFFFu, len > 0);
-  const int nit = __popc(cm);
-  const int src = lane < nit ? (int)__fns(cm, 0u, lane + 1) : 0;
-  int lenc = __shfl_sync(0xFFFFFFFFu, len, src);
-  const unsigned blo0 = __shfl_sync(0xFFFFFFFFu, (unsigned)base, src);
-  const unsigned bhi0 = __shfl_sync(0xFFFFFFFFu, (unsigned)(base >> 32), src);
-  const uint32_t infc = __shfl_sync(0xFFFFFFFFu, info, src);
-  if (lane >= nit) lenc = 0;
-  int incl = lenc;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  const int pre = incl - lenc;  // first flat slot of compact item `lane`
-  const int T = __shfl_sync(0xFFFFFFFFu, incl, 31);
-  const unsigned long long bc = (((unsigned long long)bhi0 << 32) | blo0) - (unsigned long long)pre;
-  const unsigned blo = (unsigned)bc, bhi = (unsigned)(bc >> 32);
-  const bool mine = lane < nit;
-  const unsigned le_mask = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+  return it;
+}
 
-  for (int f0 = 0; f0 < T; f0 += 128 * INFL) {
-    // the chunks' raw words: 4 per lane for F16W, 8 for F32W; padding where
-    // a lane has no chunk
-    constexpr int kWords = PREC == SNN_EXACT_F16W ? 4 : 8;
-    uint32_t raw[INFL][kWords];
-    uint32_t inf[INFL];
+// One warp streams its lanes' items, each lane its own bucket, a 32-byte
+// sector of records (F16W: 8 synapses; F32W: 4) per unit, INFL units in
+// flight.
+template <int PREC, int INFL>
+__device__ __forceinline__ void stream_items(const StepParams& P, const Item& it, uint32_t win_s,
+                                             const WinGeo& wg, uint64_t pol) {
+  const int units = it.units;
+  const uint32_t nbrow = it.nbrow;
+  const float wsign = it.wsign;
+  const int umax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)units);
+  // double buffer: the next INFL sectors are requested before the current
+  // ones are delivered (unused sectors read as weight 0)
+  uint4 cur[INFL][2], nxt[INFL][2];
+#pragma unroll
+  for (int u = 0; u < INFL; ++u) {
+    cur[u][0] = cur[u][1] = make_uint4(0u, 0u, 0u, 0u);
+    if (u < units) {
+      cur[u][0] = __ldcs(it.src + 2 * u);
+      cur[u][1] = __ldcs(it.src + 2 * u + 1);
+    }
+  }
+  for (int u0 = 0; u0 < umax; u0 += INFL) {
 #pragma unroll
     for (int u = 0; u < INFL; ++u) {
-      const int fu = f0 + u * 128;
-      inf[u] = 0u;
-#pragma unroll
-      for (int q = 0; q < kWords; ++q) raw[u][q] = kPad;
-      if (fu < T) {
-        // item of the chunk at flat slot fu + 4 * lane: the item holding fu,
-        // plus the items that start between fu and the lane's chunk
-        const int ebase = __popc(__ballot_sync(0xFFFFFFFFu, mine && pre <= fu)) - 1;
-        const int pos = (pre - fu) >> 2;
-        const unsigned bit = (mine && pre > fu && pos < 32) ? (1u << pos) : 0u;
-        const unsigned starts = __reduce_or_sync(0xFFFFFFFFu, bit);
-        const int e = ebase + __popc(starts & le_mask);
-        const unsigned bl = __shfl_sync(0xFFFFFFFFu, blo, e);
-        const unsigned bh = __shfl_sync(0xFFFFFFFFu, bhi, e);
-        inf[u] = __shfl_sync(0xFFFFFFFFu, infc, e);
-        const int f = fu + 4 * lane;
-        if (f < T) {
-          const long long slot = (long long)(((unsigned long long)bh << 32) | bl) + f;
-          if (PREC == SNN_EXACT_F16W) {
-            const uint4 r = __ldcs(reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(P.syn) + slot));
-            raw[u][0] = r.x;
-            raw[u][1] = r.y;
-            raw[u][2] = r.z;
-            raw[u][3] = r.w;
-          } else {
-            const uint4* p4 = reinterpret_cast<const uint4*>(static_cast<const uint2*>(P.syn) + slot);
-            const uint4 r0 = __ldcs(p4);
-            const uint4 r1 = __ldcs(p4 + 1);
-            raw[u][0] = r0.x; raw[u][1] = r0.y; raw[u][2] = r0.z; raw[u][3] = r0.w;
-            raw[u][4] = r1.x; raw[u][5] = r1.y; raw[u][6] = r1.z; raw[u][7] = r1.w;
-          }
-        }
+      const int un = u0 + INFL + u;
+      nxt[u][0] = nxt[u][1] = make_uint4(0u, 0u, 0u, 0u);
+      if (un < units) {
+        nxt[u][0] = __ldcs(it.src + 2 * un);
+        nxt[u][1] = __ldcs(it.src + 2 * un + 1);
       }
     }
 #pragma unroll
     for (int u = 0; u < INFL; ++u) {
 #pragma unroll
-      for (int qd = 0; qd < 4; ++qd) {
+      for (int h = 0; h < 2; ++h) {
+        const uint4 r = cur[u][h];
         if (PREC == SNN_EXACT_F16W) {
-          const uint32_t w = raw[u][qd];
-          deliver_record<PREC>(w == kPad ? kPad : (w & 0x1FFFFu), w >> 17, inf[u], win_s, wbase,
-                               wlen, pol, nb, P);
+          deliver_f16(r.x, nbrow, wsign, P, pol);
+          deliver_f16(r.y, nbrow, wsign, P, pol);
+          deliver_f16(r.z, nbrow, wsign, P, pol);
+          deliver_f16(r.w, nbrow, wsign, P, pol);
         } else {
-          deliver_record<PREC>(raw[u][2 * qd], raw[u][2 * qd + 1], inf[u], win_s, wbase, wlen,
-                               pol, nb, P);
+          deliver_f32(r.x, (int32_t)r.y, wg, win_s, P, pol);
+          deliver_f32(r.z, (int32_t)r.w, wg, win_s, P, pol);
         }
       }
+    }
+#pragma unroll
+    for (int u = 0; u < INFL; ++u) {
+      cur[u][0] = nxt[u][0];
+      cur[u][1] = nxt[u][1];
     }
   }
 }
 
-// Delivery block vb of vgrid for step t.  The step's items, ordered by
-// (column, delay bucket, spiker), are split into vgrid equal contiguous
-// ranges; block vb locates the first and last column of its range from the
-// group and column counts (gsum, isum), tabulates the (column, bucket) counts
-// of those columns (in pieces of at most kTabEntries entries) and lets its
-// warps take batches of kBatchItems items.  With P.agg the synapses onto the
-// first kWindows columns of each piece, from any of the piece's items, are
-// summed in shared memory (win_base, kWindows * n_per_col ints) and flushed
-// once per piece.
-template <int PREC, int INFL>
+// Delivery block vb of vgrid (NT threads) for step t.  The step's items,
+// ordered by (virtual column, delay bucket, spiker), are split into at most
+// vgrid equal contiguous ranges of at least kMinItems items; block vb
+// locates the first and last virtual column of its range from the group and
+// column counts (gsum, isum) and walks the tiles it meets.  For each tile
+// part it tabulates the (column, bucket) counts, builds the F16W neighbour
+// table, lets its warps take batches of kBatchItems items, and flushes the
+// tile's window.  Counts that disagree with the spike lists set the status
+// word instead of being delivered.  `dyn` is the block's dynamic shared
+// memory: table, neighbour table, window.
+template <int PREC, int INFL, int NT>
 __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, int vb, int vgrid,
-                                             DeliverSmem& S, int32_t* win_base, uint32_t* nb) {
+                                             DeliverSmem& S, unsigned char* dyn) {
   __syncthreads();  // the shared memory may still be read by a previous body
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  unsigned* tab = reinterpret_cast<unsigned*>(dyn);
+  uint32_t* nb = tab + tab_words(P);
+  int32_t* win = reinterpret_cast<int32_t*>(nb + nb_words<PREC>(P));
   // the slot that the next update fills holds step t - d_max: no longer read
   const long long next_slot = (t + 1) % P.nslot;
-  if (vb == 0 && threadIdx.x == 0) P.cnt[next_slot] = 0u;
-  for (long long c = (long long)vb * blockDim.x + threadIdx.x; c < P.ncol;
-       c += (long long)vgrid * blockDim.x)
+  if (vb == 0 && tid == 0) P.cnt[next_slot] = 0u;
+  for (long long c = (long long)vb * NT + tid; c < P.ncol; c += (long long)vgrid * NT)
     P.ccnt[next_slot * P.ncol + c] = 0u;
-  if (P.agg)
-    for (int l = threadIdx.x; l < kWindows * P.npc; l += blockDim.x) win_base[l] = 0;
-  if (threadIdx.x < kMaxDelays) {
-    const int b = threadIdx.x;
+  if (tid < kMaxDelays) {
+    const int b = tid;
     const long long s = t + 1 - (P.dmin + b);
     S.slot[b] = (b < P.ndel && s >= 0) ? (int)(s % P.nslot) : -1;
   }
-  if (threadIdx.x == 0) {
-    S.c0 = -1;
-    S.c1 = -1;
+  if (tid == 0) {
+    S.v0 = -1;
+    S.v1 = -1;
+    S.xg[0] = S.xg[1] = -1;
     S.next = 0u;
   }
 
   // the block's item range, from the group counts
   const int ngrp = (P.ncol + 31) >> 5;
-  const int per = (ngrp + (int)blockDim.x - 1) / (int)blockDim.x;
-  const int g0 = threadIdx.x * per;
+  const int per = (ngrp + NT - 1) / NT;
+  const int g0 = tid * per;
   unsigned long long mine = 0ull;
   for (int g = g0; g < g0 + per && g < ngrp; ++g) mine += P.gsum[g];
   unsigned long long total = 0ull;
   const unsigned long long excl = block_scan(mine, S, &total);
-  const unsigned long long lo = total * (unsigned long long)vb / (unsigned long long)vgrid;
-  const unsigned long long hi = total * (unsigned long long)(vb + 1) / (unsigned long long)vgrid;
+  const unsigned long long want = (total + kMinItems - 1) / kMinItems;
+  const int nact = (int)(want < (unsigned long long)vgrid ? (want ? want : 1ull) : (unsigned long long)vgrid);
+  if (vb >= nact) return;
+  const unsigned long long lo = total * (unsigned long long)vb / (unsigned long long)nact;
+  const unsigned long long hi = total * (unsigned long long)(vb + 1) / (unsigned long long)nact;
   if (lo >= hi) return;
   for (int i = 0; i < 2; ++i) {
     const unsigned long long x = i == 0 ? lo : hi - 1;
@@ -571,8 +707,8 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
     }
   }
   __syncthreads();
-  // the columns holding lo and hi - 1, from the column counts of their groups
-  if (warp < 2) {
+  // the virtual columns holding lo and hi - 1, from the column counts of their groups
+  if (warp < 2 && S.xg[warp] >= 0) {
     const unsigned long long x = warp == 0 ? lo : hi - 1;
     const int c = S.xg[warp] * 32 + lane;
     const unsigned v = c < P.ncol ? P.isum[c] : 0u;
@@ -585,98 +721,152 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
     const unsigned long long pos = S.xgp[warp] + incl - v;
     if (c < P.ncol && x >= pos && x < pos + v) {
       if (warp == 0) {
-        S.c0 = c;
+        S.v0 = c;
         S.p0 = pos;
       } else {
-        S.c1 = c;
+        S.v1 = c;
       }
     }
   }
   __syncthreads();
-  const int c0 = S.c0, c1 = S.c1;
-  if (c0 < 0 || c1 < c0) return;  // inconsistent counts: nothing is delivered
+  const int v0 = S.v0, v1 = S.v1;
+  if (v0 < 0 || v1 < v0) {
+    if (tid == 0) set_status(P, kStatusCounts);
+    return;
+  }
 
   const uint64_t pol = evict_last_policy();
-  const uint32_t win_s = (uint32_t)__cvta_generic_to_shared(win_base);
-  // a piece tabulates at most 4 entries per thread and kPieceCols columns
-  const int cols_per_piece = min(min(kTabEntries, 4 * (int)blockDim.x) / P.ndel, kPieceCols);
-  unsigned long long pbase = S.p0;  // items before the piece's first column
-  for (int pc = c0; pc <= c1; pc += cols_per_piece) {
-    const int ncp = min(cols_per_piece, c1 - pc + 1);
-    const int n_entries = ncp * P.ndel;
-    // tabulate the piece: 4 consecutive entries per thread
-    unsigned v4[4];
-    unsigned sum4 = 0u;
+  const uint32_t win_s = (uint32_t)__cvta_generic_to_shared(win);
+  const uint32_t nb_s = (uint32_t)__cvta_generic_to_shared(nb);
+  unsigned long long pbase = S.p0;  // items before the tile part's first column
+  bool win_zero = false;            // the window has been cleared in this body
+  for (int v = v0; v <= v1;) {
+    const TileGeo g = tile_geo(P, v);
+    const int ve = min(v1, g.first + g.tw * g.th - 1);
+    const int ncv = ve - v + 1;
+    const int n_entries = ncv * P.ndel;
+    for (int k = tid; k < ncv; k += NT) {
+      const int c = (int)P.vcol[v + k];
+      const int cy = c / P.W;
+      S.ccol[k] = c;
+      S.cx[k] = c - cy * P.W;
+      S.cy[k] = cy;
+    }
+    __syncthreads();
+    // tabulate the tile part: consecutive entries per thread
+    constexpr int kEpt = (kMaxTileCols * kMaxDelays + NT - 1) / NT;
+    const int ept = (n_entries + NT - 1) / NT;
+    unsigned cnt[kEpt];
+    unsigned sum = 0u;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x * 4 + q;
-      unsigned v = 0u;
-      if (e < n_entries) {
+    for (int q = 0; q < kEpt; ++q) {
+      const int e = tid * ept + q;
+      unsigned c = 0u;
+      if (q < ept && e < n_entries) {
         const int k = e / P.ndel;
         const int sl = S.slot[e - k * P.ndel];
-        v = sl >= 0 ? P.ccnt[(long long)sl * P.ncol + pc + k] : 0u;
+        c = sl >= 0 ? P.ccnt[(long long)sl * P.ncol + S.ccol[k]] : 0u;
+        c = min(c, (unsigned)P.npc);  // a column lists at most n_per_col spikes
       }
-      v4[q] = v;
-      sum4 += v;
+      cnt[q] = c;
+      sum += c;
     }
     unsigned long long ptotal = 0ull;
-    unsigned run = (unsigned)block_scan(sum4, S, &ptotal);
+    unsigned run = (unsigned)block_scan(sum, S, &ptotal);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x * 4 + q;
-      if (e < n_entries) S.tab[e] = run;
-      run += v4[q];
+    for (int q = 0; q < kEpt; ++q) {
+      const int e = tid * ept + q;
+      if (q < ept && e < n_entries) tab[e] = run;
+      run += cnt[q];
     }
-    if (threadIdx.x == 0) S.tab[n_entries] = (unsigned)ptotal;
-    __syncthreads();
+    if (tid == 0) tab[n_entries] = (unsigned)ptotal;
+    // the block's items of this part; a part with few items skips the window
+    // (clearing and flushing it would cost more than it saves)
     const unsigned a = lo > pbase ? (unsigned)(lo - pbase) : 0u;
     const unsigned b = hi > pbase ? (unsigned)min(hi - pbase, ptotal) : 0u;
-    if (PREC == SNN_EXACT_F16W) {
-      // first neuron of the column at each stencil offset of each column of
-      // the piece (periodic), for the records' column-relative targets
-      for (int m = threadIdx.x; m < ncp * 64; m += blockDim.x) {
-        const int c = pc + (m >> 6), off = m & 63;
-        const int cy = c / P.W, cx = c - cy * P.W;
-        const int ty = wrap(cy + (off >> 3) - 3, P.H), tx = wrap(cx + (off & 7) - 3, P.W);
-        nb[m] = ((uint32_t)ty * (uint32_t)P.W + (uint32_t)tx) * (uint32_t)P.npc;
-      }
-      __syncthreads();
+    const bool windowed = P.agg && b > a && b - a >= kWinMinItems;
+    const WinGeo wg = win_geo(P, g, windowed);
+    if (windowed && !win_zero) {
+      for (int i = tid; i < (P.win_cap >> 2); i += NT) reinterpret_cast<int4*>(win)[i] = make_int4(0, 0, 0, 0);
+      win_zero = true;
     }
-    // windows: the piece's first columns, for synapses from any of its items
-    const uint32_t wbase = (uint32_t)pc * (uint32_t)P.npc;
-    const uint32_t wlen = P.agg ? (uint32_t)min(kWindows, ncp) * (uint32_t)P.npc : 0u;
-    while (a < b) {
-      unsigned k0 = 0u;
-      if (lane == 0) k0 = atomicAdd(&S.next, (unsigned)kBatchItems);
-      k0 = __shfl_sync(0xFFFFFFFFu, k0, 0);
-      if (a + k0 >= b) break;
-      const unsigned end = min(b, a + k0 + (unsigned)kBatchItems);
-      deliver_batch<PREC, INFL>(P, lane < kBatchItems ? a + k0 + lane : end, end, S, n_entries, pc,
-                                win_s, wbase, wlen, pol, nb);
+    for (int m = tid; m < wg.ww * wg.wh; m += NT) {
+      const int ry = m / wg.ww, rx = m - ry * wg.ww;
+      int x = wg.x0 + rx, y = wg.y0 + ry;
+      x -= x >= P.W ? P.W : 0;
+      y -= y >= P.H ? P.H : 0;
+      S.wbase[m] = ((uint32_t)y * (uint32_t)P.W + (uint32_t)x) * (uint32_t)P.npc;
+    }
+    if (PREC == SNN_EXACT_F16W && b > a) {
+      // the column at each stencil offset of each column of the part: its
+      // shared-window address, or bit 31 set and its first neuron in the
+      // accumulator (offsets with dx + 3 = 7 belong to padding records)
+      for (int m = tid; m < ncv * 64; m += NT) {
+        const int k = m >> 6, off = m & 63;
+        const int tx = wrap(S.cx[k] + (off & 7) - 3, P.W);
+        const int ty = wrap(S.cy[k] + (off >> 3) - 3, P.H);
+        int rx = tx - wg.x0;
+        rx += rx < 0 ? P.W : 0;
+        int ry = ty - wg.y0;
+        ry += ry < 0 ? P.H : 0;
+        nb[m] = (rx < wg.ww && ry < wg.wh)
+                    ? win_s + 4u * (((uint32_t)ry * (uint32_t)wg.ww + (uint32_t)rx) * (uint32_t)P.npc)
+                    : 0x80000000u | (((uint32_t)ty * (uint32_t)P.W + (uint32_t)tx) * (uint32_t)P.npc);
+      }
     }
     __syncthreads();
-    // flush the windows with coalesced reductions, leaving them zeroed
-    for (uint32_t m = threadIdx.x; m < wlen; m += blockDim.x) {
-      const int32_t v = win_base[m];
-      if (v) {
-        red_add(P.acc + wbase + m, v, pol);
-        win_base[m] = 0;
+    // the counts of each column must equal the items the range assumed
+    if (tid < ncv && tab[(tid + 1) * P.ndel] - tab[tid * P.ndel] != P.isum[v + tid])
+      set_status(P, kStatusCounts);
+    // warps claim batches of kBatchItems items; a warp resolves its next
+    // batch (descriptor loads) before it streams the current one
+    if (a < b) {
+      unsigned k0 = 0u;
+      if (lane == 0) k0 = atomicAdd(&S.next, (unsigned)kBatchItems);
+      k0 = a + __shfl_sync(0xFFFFFFFFu, k0, 0);
+      Item cur = resolve_item<PREC>(P, k0 + lane, b, S, tab, n_entries, nb_s);
+      while (k0 < b) {
+        unsigned k1 = 0u;
+        if (lane == 0) k1 = atomicAdd(&S.next, (unsigned)kBatchItems);
+        k1 = a + __shfl_sync(0xFFFFFFFFu, k1, 0);
+        const Item nxt = resolve_item<PREC>(P, k1 + lane, b, S, tab, n_entries, nb_s);
+        stream_items<PREC, INFL>(P, cur, win_s, wg, pol);
+        cur = nxt;
+        k0 = k1;
       }
     }
-    if (threadIdx.x == 0) S.next = 0u;
+    __syncthreads();
+    // flush the window with coalesced reductions, leaving it zeroed: word
+    // m is neuron l of slot s; (s, l) advance with m
+    const uint32_t wlen = (uint32_t)(wg.ww * wg.wh) * (uint32_t)P.npc;
+    uint32_t fs = div_by((uint32_t)tid, (uint32_t)P.npc, P.npc_m);
+    uint32_t fl = (uint32_t)tid - fs * (uint32_t)P.npc;
+    for (uint32_t m = tid; m < wlen; m += NT) {
+      const int32_t x = win[m];
+      if (x) {
+        red_add(P.acc + S.wbase[fs] + fl, x, pol);
+        win[m] = 0;
+      }
+      fl += NT;
+      while (fl >= (uint32_t)P.npc) {
+        fl -= (uint32_t)P.npc;
+        ++fs;
+      }
+    }
+    if (tid == 0) S.next = 0u;
     pbase += ptotal;
+    v = ve + 1;
     __syncthreads();
   }
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepParams P) {
-  extern __shared__ int32_t s_win[];  // [kWindows][n_per_col] when P.agg
+__global__ void __launch_bounds__(kDeliverThreads, 1) deliver_kernel(const StepParams P) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ DeliverSmem S;
-  __shared__ uint32_t s_nb[PREC == SNN_EXACT_F16W ? kNbEntries : 1];
   const long long t = P.ctl->t;
-  deliver_body<PREC, PREC == SNN_EXACT_F16W ? kInflightF16 : kInflight>(
-      P, t, (int)blockIdx.x, (int)gridDim.x, S, s_win, s_nb);
+  deliver_body<PREC, PREC == SNN_EXACT_F16W ? kInflightF16 : kInflightF32, kDeliverThreads>(
+      P, t, (int)blockIdx.x, (int)gridDim.x, S, s_dyn);
 
   // the last block to finish closes the step
   __syncthreads();
@@ -693,11 +883,12 @@ __global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(const StepPara
 
 // ---------------------------------------------------------------------------
 // Batched form: many independent nets advanced by one persistent launch.
-// Every step runs the update blocks of all nets, a grid barrier, the delivery
-// blocks of all nets, and a second barrier.  Virtual block g of a phase
-// belongs to net k with first[k] <= g < first[k + 1]; each virtual block is the
-// standalone kernel's block, so every net computes exactly what its own
-// kernels compute.
+// Every step runs the update bodies of all nets (four 256-thread sub-blocks
+// per block, each with its own named barrier), a grid barrier, the delivery
+// bodies of all nets (whole blocks), and a second barrier.  Virtual body g of
+// a phase belongs to net k with first[k] <= g < first[k + 1]; each virtual
+// body is the standalone kernel's block body, so every net computes exactly
+// what its own kernels compute.
 // ---------------------------------------------------------------------------
 
 // Bounded grid barrier (all blocks are co-resident: cooperative launch).  A
@@ -742,7 +933,7 @@ __device__ __forceinline__ bool grid_barrier(const BatchParams& B, unsigned* s_o
   return *s_ok != 0u;
 }
 
-// Net of virtual block g: the last k with first[k] <= g.
+// Net of virtual body g: the last k with first[k] <= g.
 __device__ __forceinline__ int net_of(const int* first, int n, int g) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -756,15 +947,15 @@ __device__ __forceinline__ int net_of(const int* first, int n, int g) {
 }
 
 template <int PREC, int INFL>
-__global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchParams B) {
+__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(const BatchParams B) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
-  __shared__ StepParams s_p;  // the current virtual block's net
-  __shared__ uint32_t s_nb[PREC == SNN_EXACT_F16W ? kNbEntries : 1];
+  __shared__ StepParams s_p[kUpdateSubs];  // the nets of the current virtual bodies
+  __shared__ DeliverSmem SD;
   __shared__ int s_uf[kMaxBatch + 1], s_df[kMaxBatch + 1];
   __shared__ unsigned s_ok;
-  UpdateSmem& SU = *reinterpret_cast<UpdateSmem*>(s_dyn);
-  DeliverSmem& SD = *reinterpret_cast<DeliverSmem*>(s_dyn);
-  int32_t* win = reinterpret_cast<int32_t*>(s_dyn + kDeliverSmemPad);
+  UpdateSmem* SU = reinterpret_cast<UpdateSmem*>(s_dyn);  // one per sub-block
+  const int sub = threadIdx.x / kUpdateThreads;
+  const int stid = threadIdx.x - sub * kUpdateThreads;
   const int n = B.n_nets;
   for (int k = threadIdx.x; k <= n; k += blockDim.x) {
     s_uf[k] = B.u_first[k];
@@ -772,24 +963,26 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchPara
   }
   __syncthreads();
   const int total_u = s_uf[n], total_d = s_df[n];
+  constexpr int kParamWords = (int)(sizeof(StepParams) / 4);
   for (long long step = 0; step < B.n_steps; ++step) {
     const long long t = B.t0 + step;
-    for (int g = blockIdx.x; g < total_u; g += gridDim.x) {
+    for (int g = blockIdx.x * kUpdateSubs + sub; g < total_u; g += gridDim.x * kUpdateSubs) {
       const int k = net_of(s_uf, n, g);
-      __syncthreads();
-      for (int w = threadIdx.x; w < (int)(sizeof(StepParams) / 4); w += blockDim.x)
-        reinterpret_cast<uint32_t*>(&s_p)[w] = reinterpret_cast<const uint32_t*>(B.nets + k)[w];
-      __syncthreads();
-      update_body(s_p, t, g - s_uf[k], s_uf[k + 1] - s_uf[k], SU);
+      body_sync(1 + sub);
+      for (int w = stid; w < kParamWords; w += kUpdateThreads)
+        reinterpret_cast<uint32_t*>(&s_p[sub])[w] = reinterpret_cast<const uint32_t*>(B.nets + k)[w];
+      body_sync(1 + sub);
+      update_body(s_p[sub], t, g - s_uf[k], s_uf[k + 1] - s_uf[k], SU[sub], stid, 1 + sub);
     }
     if (!grid_barrier(B, &s_ok)) return;
     for (int g = blockIdx.x; g < total_d; g += gridDim.x) {
       const int k = net_of(s_df, n, g);
       __syncthreads();
-      for (int w = threadIdx.x; w < (int)(sizeof(StepParams) / 4); w += blockDim.x)
-        reinterpret_cast<uint32_t*>(&s_p)[w] = reinterpret_cast<const uint32_t*>(B.nets + k)[w];
+      for (int w = threadIdx.x; w < kParamWords; w += blockDim.x)
+        reinterpret_cast<uint32_t*>(&s_p[0])[w] = reinterpret_cast<const uint32_t*>(B.nets + k)[w];
       __syncthreads();
-      deliver_body<PREC, INFL>(s_p, t, g - s_df[k], s_df[k + 1] - s_df[k], SD, win, s_nb);
+      deliver_body<PREC, INFL, kBatchThreads>(s_p[0], t, g - s_df[k], s_df[k + 1] - s_df[k], SD,
+                                              s_dyn);
     }
     if (!grid_barrier(B, &s_ok)) return;
   }
@@ -919,31 +1112,36 @@ cudaError_t launch_update(const StepParams& p, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-size_t deliver_smem(int npc, bool agg) {
-  return agg ? (size_t)kWindows * (size_t)npc * sizeof(int32_t) : 0u;
+size_t deliver_smem(const StepParams& p, int precision) {
+  const size_t tabw = ((size_t)p.tile * p.tile * p.ndel + 1 + 3) & ~(size_t)3;
+  const size_t nbw = precision == SNN_EXACT_F16W ? (size_t)p.tile * p.tile * 64 : 0;
+  return (tabw + nbw + (size_t)p.win_cap) * 4;
 }
 
-// Delivery grid: a persistent grid at full occupancy.
-int deliver_grid(int precision, int num_sms, int npc, bool agg) {
-  const size_t smem = deliver_smem(npc, agg);
+int deliver_threads() { return kDeliverThreads; }
+
+// Delivery grid: one block per SM (a persistent grid).
+int deliver_grid(const StepParams& p, int precision, int num_sms) {
+  const size_t smem = deliver_smem(p, precision);
   int per_sm = 0;
   if (precision == SNN_EXACT_F16W) {
-    cudaFuncSetAttribute(deliver_kernel<SNN_EXACT_F16W>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaFuncSetAttribute(deliver_kernel<SNN_EXACT_F16W>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, deliver_kernel<SNN_EXACT_F16W>,
                                                   kDeliverThreads, smem);
   } else {
-    cudaFuncSetAttribute(deliver_kernel<SNN_EXACT_F32W>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaFuncSetAttribute(deliver_kernel<SNN_EXACT_F32W>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, deliver_kernel<SNN_EXACT_F32W>,
                                                   kDeliverThreads, smem);
   }
-  if (per_sm < 1) per_sm = 1;
   return per_sm * num_sms;
 }
 
 cudaError_t launch_deliver(const StepParams& p, int precision, int grid, cudaStream_t st) {
-  const size_t smem = deliver_smem(p.npc, p.agg != 0);
+  const size_t smem = deliver_smem(p, precision);
   if (precision == SNN_EXACT_F16W)
     deliver_kernel<SNN_EXACT_F16W><<<grid, kDeliverThreads, smem, st>>>(p);
   else
@@ -972,26 +1170,25 @@ void* batch_kernel_ptr(int precision, int infl) {
 }
 }  // namespace
 
-size_t batch_smem(int max_npc) {
-  const size_t upd = sizeof(UpdateSmem);
-  const size_t del = kDeliverSmemPad + (size_t)kWindows * (size_t)max_npc * sizeof(int32_t);
-  return upd > del ? upd : del;
+size_t batch_smem(size_t max_deliver_smem) {
+  const size_t upd = kUpdateSubs * sizeof(UpdateSmem);
+  return upd > max_deliver_smem ? upd : max_deliver_smem;
 }
 
-int batch_grid(int precision, int infl, int num_sms, int max_npc) {
-  const size_t smem = batch_smem(max_npc);
+int batch_grid(int precision, int infl, int num_sms, size_t smem) {
   void* fn = batch_kernel_ptr(precision, infl);
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, smem);
   return per_sm * num_sms;
 }
 
-cudaError_t launch_batch(const BatchParams& b, int precision, int infl, int grid, int max_npc,
+cudaError_t launch_batch(const BatchParams& b, int precision, int infl, int grid, size_t smem,
                          cudaStream_t st) {
   void* args[] = {const_cast<BatchParams*>(&b)};
   return cudaLaunchCooperativeKernel(batch_kernel_ptr(precision, infl), dim3(grid),
-                                     dim3(kBatchThreads), args, batch_smem(max_npc), st);
+                                     dim3(kBatchThreads), args, smem, st);
 }
 
 cudaError_t launch_sum_parts(const unsigned long long* part, int n, unsigned long long* out,
