@@ -188,6 +188,18 @@ int snn_read_synapses(snn_net* net, int64_t j0, int64_t n, int64_t* target,
 int snn_row_lengths(snn_net* net, int64_t j0, int64_t n, int32_t* counts);
 
 /*
+ * snn_debug_offset_count -- testing aid with no counterpart in the paper: adds
+ * delta to the number of delivery items the library has counted for `column`
+ * (0 <= column < grid_w * grid_h) and to the count of its group of 32
+ * columns, or to the group count only when group_only is nonzero, as a
+ * bookkeeping fault would.  The spike lists are left as they are, so the next
+ * delivery finds counts that disagree with them and must set the net's status
+ * word (see snn_step).  Synchronises the net's stream.  SNN_EINVAL for a
+ * column out of range.
+ */
+int snn_debug_offset_count(snn_net* net, int64_t column, int32_t delta, int32_t group_only);
+
+/*
  * snn_info -- sizes of the net: info[0] = N neurons, [1] = synapses,
  * [2] = device bytes held, [3] = bytes of the synapse table, [4] = row
  * capacity in synapse slots, [5] = precision, [6] = side of the delivery
@@ -208,11 +220,10 @@ int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes);
 /*
  * snn_update_noalloc -- one neuron-update step on buffers the caller owns,
  * allocating nothing.  The paper has no counterpart: this entry point exists
- * for callers that cannot let a library call cudaMalloc -- a loop being
- * recorded into a CUDA graph (allocation is not allowed during stream
- * capture), a process whose device memory is already reserved by another
- * framework's allocator or a fixed arena, or a real-time loop that cannot
- * afford an allocation's implicit synchronisation.
+ * for callers that cannot let a library call cudaMalloc -- a process whose
+ * device memory is already reserved by another framework's allocator or a
+ * fixed arena, or a real-time loop that cannot afford an allocation's
+ * implicit synchronisation.
  *
  * It runs the same update kernel as snn_step for step `step` of a
  * grid_w x grid_h network of N = grid_w * grid_h * n_per_col neurons (the
@@ -224,8 +235,10 @@ int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes);
  *   refractory    u8, 4-byte aligned: remaining refractory steps, in/out;
  *   input         int32, 16-byte aligned: recurrent input of this step in
  *                 2^-16 mV units, read and then cleared to zero;
- *   spikes        u32[N]: receives the indices of the neurons that fired;
- *   col_counts    u64[2 * columns] or NULL: spikes per column (E, I).
+ *   spikes        u32[N], 4-byte aligned: receives the indices of the
+ *                 neurons that fired;
+ *   col_counts    u64[2 * columns], 8-byte aligned, or NULL: spikes per
+ *                 column (E, I).
  * Host outputs: *n_spikes (entries written to spikes), *ext_events (sum of
  * the external Poisson counts; may be NULL).  Synchronises cuda_stream
  * (a cudaStream_t; NULL is the legacy default stream).
@@ -236,8 +249,10 @@ int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes);
  * array and clears what it needs at its start, so calls whose GPU work
  * overlaps (on different streams or threads) race and must be serialised by
  * the caller.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before capturing a
- * stream.  Returns SNN_EINVAL for bad parameters, sizes or alignment,
+ * address (cudaGetSymbolAddress) and keeps it for the life of the process;
+ * make that first call before any stream capture begins, and do not reset
+ * the device (cudaDeviceReset) between calls, which would invalidate the kept
+ * address.  Returns SNN_EINVAL for bad parameters, sizes or alignment,
  * SNN_ECUDA for a CUDA error (message in snn_last_error(NULL)).
  */
 int snn_update_noalloc(int grid_w, int grid_h, const snn_neuron_params* neuron,

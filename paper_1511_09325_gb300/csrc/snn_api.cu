@@ -929,6 +929,25 @@ const char* snn_last_error(const snn_net* net) {
   return net ? net->err.c_str() : g_err.c_str();
 }
 
+int snn_debug_offset_count(snn_net* net, int64_t column, int32_t delta, int32_t group_only) {
+  if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
+  if (column < 0 || column >= net->ncol) return fail(net, SNN_EINVAL, "column out of range");
+  int rc = sync(net);
+  if (rc) return rc;
+  uint32_t v = 0u;
+  SNN_CUDA(net, cudaMemcpy(&v, net->colv + column, 4, cudaMemcpyDeviceToHost));
+  unsigned word = 0u;
+  if (!group_only) {
+    SNN_CUDA(net, cudaMemcpy(&word, net->isum + v, 4, cudaMemcpyDeviceToHost));
+    word += (unsigned)delta;
+    SNN_CUDA(net, cudaMemcpy(net->isum + v, &word, 4, cudaMemcpyHostToDevice));
+  }
+  SNN_CUDA(net, cudaMemcpy(&word, net->gsum + (v >> 5), 4, cudaMemcpyDeviceToHost));
+  word += (unsigned)delta;
+  SNN_CUDA(net, cudaMemcpy(net->gsum + (v >> 5), &word, 4, cudaMemcpyHostToDevice));
+  return SNN_OK;
+}
+
 void snn_destroy(snn_net* net) {
   if (!net) return;
   if (net->stream) cudaStreamSynchronize(net->stream);

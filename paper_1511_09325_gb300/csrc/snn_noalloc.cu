@@ -1,11 +1,10 @@
 // snn_noalloc.cu -- one neuron-update step on caller-owned buffers, with no
 // allocation of any kind.
 //
-// Some callers cannot let a library call cudaMalloc: a loop being recorded
-// into a CUDA graph (allocation calls are not allowed while a stream is
-// captured), a process whose device memory is already reserved by another
-// framework's caching allocator or a fixed arena, or a real-time loop that
-// cannot afford the implicit synchronisation of an allocation.  For them the
+// Some callers cannot let a library call cudaMalloc: a process whose device
+// memory is already reserved by another framework's caching allocator or a
+// fixed arena, or a real-time loop that cannot afford the implicit
+// synchronisation of an allocation.  For them the
 // neuron-update kernel of snn_step.cu runs here on their own state arrays; its
 // scratch (step counter, spike-list cursor, per-block partial sums and the
 // per-column spike counters) lives in one file-scope device array below, of a
@@ -42,7 +41,8 @@ std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on `dev` (which must be current).  The
-// first call on a device looks it up; later calls reuse it.
+// first call on a device looks it up; later calls reuse it, which assumes the
+// device is not reset (cudaDeviceReset reloads the module) in between.
 int scratch_address(int dev, unsigned char** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (dev < 0 || dev >= kMaxDevices) return fail_global(SNN_EINVAL, "device ordinal out of range");
@@ -76,8 +76,11 @@ extern "C" int snn_update_noalloc(int grid_w, int grid_h, const snn_neuron_param
   if (step < 0 || step > 0xFFFFFFFFLL) return fail_global(SNN_EINVAL, "step must be in 0..2^32-1");
   if (!v || !c || !refractory || !input || !spikes || !n_spikes)
     return fail_global(SNN_EINVAL, "null buffer");
-  if (!aligned(v, 16) || !aligned(c, 16) || !aligned(input, 16) || !aligned(refractory, 4))
-    return fail_global(SNN_EINVAL, "v, c, input must be 16-byte and refractory 4-byte aligned");
+  if (!aligned(v, 16) || !aligned(c, 16) || !aligned(input, 16) || !aligned(refractory, 4) ||
+      !aligned(spikes, 4) || !aligned(col_counts, 8))
+    return fail_global(SNN_EINVAL,
+                       "v, c, input must be 16-byte, refractory and spikes 4-byte, col_counts "
+                       "8-byte aligned");
 
   HostTables tb;
   int rc = make_neuron_tables(*neuron, &tb, &why);

@@ -739,7 +739,8 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
   const uint32_t win_s = (uint32_t)__cvta_generic_to_shared(win);
   const uint32_t nb_s = (uint32_t)__cvta_generic_to_shared(nb);
   unsigned long long pbase = S.p0;  // items before the tile part's first column
-  bool win_zero = false;            // the window has been cleared in this body
+  unsigned long long covered = 0ull;  // items of the range found in the spike lists
+  bool win_zero = false;              // the window has been cleared in this body
   for (int v = v0; v <= v1;) {
     const TileGeo g = tile_geo(P, v);
     const int ve = min(v1, g.first + g.tw * g.th - 1);
@@ -784,6 +785,7 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
     // (clearing and flushing it would cost more than it saves)
     const unsigned a = lo > pbase ? (unsigned)(lo - pbase) : 0u;
     const unsigned b = hi > pbase ? (unsigned)min(hi - pbase, ptotal) : 0u;
+    covered += b > a ? b - a : 0u;
     const bool windowed = P.agg && b > a && b - a >= kWinMinItems;
     const WinGeo wg = win_geo(P, g, windowed);
     if (windowed && !win_zero) {
@@ -858,6 +860,8 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
     v = ve + 1;
     __syncthreads();
   }
+  // every item of the range must have been found in the spike lists
+  if (tid == 0 && covered != hi - lo) set_status(P, kStatusCounts);
 }
 
 template <int PREC>

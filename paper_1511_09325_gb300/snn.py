@@ -22,6 +22,7 @@ PRECISIONS = {"f32w": SNN_EXACT_F32W, "f16w": SNN_EXACT_F16W}
 EXPORTS = ("snn_build", "snn_step", "snn_read_spikes", "snn_pending_spikes",
            "snn_set_record_capacity", "snn_read_rates", "snn_stats", "snn_get_state",
            "snn_read_synapses", "snn_row_lengths", "snn_info", "snn_step_profiled", "snn_update_noalloc",
+           "snn_debug_offset_count",
            "snn_batch_build", "snn_batch_step", "snn_batch_net", "snn_batch_tune",
            "snn_batch_set_wait", "snn_batch_last_error", "snn_batch_destroy",
            "snn_grad_build", "snn_grad_run", "snn_grad_last_error", "snn_grad_destroy",
@@ -80,6 +81,7 @@ def load(path=LIB_PATH):
     L.snn_row_lengths.argtypes = [vp, i64, i64, vp]
     L.snn_info.argtypes = [vp, vp, i32]
     L.snn_step_profiled.argtypes = [vp, i64, vp, vp]
+    L.snn_debug_offset_count.argtypes = [vp, i64, ctypes.c_int32, ctypes.c_int32]
     L.snn_update_noalloc.argtypes = [i32, i32, P(NeuronParams), ctypes.c_uint64, i64,
                                      vp, vp, vp, vp, vp, P(i64), P(i64), vp, vp]
     L.snn_batch_build.argtypes = [i32, vp, vp, vp, vp, vp, i32, vp, P(vp)]
@@ -239,10 +241,17 @@ def snn_read_synapses(handle, j0, n, k_out=None):
 
 
 def snn_info(handle):
-    info = np.zeros(6, np.int64)
-    _check(load().snn_info(handle, _p(info), 6), handle)
-    keys = ("neurons", "synapses", "device_bytes", "synapse_bytes", "row_capacity", "precision")
+    info = np.zeros(9, np.int64)
+    _check(load().snn_info(handle, _p(info), 9), handle)
+    keys = ("neurons", "synapses", "device_bytes", "synapse_bytes", "row_capacity", "precision",
+            "tile", "deliver_blocks", "update_blocks")
     return dict(zip(keys, (int(x) for x in info)))
+
+
+def snn_debug_offset_count(handle, column, delta, group_only=False):
+    """Testing aid: offset one column's delivery item count (see snn.h)."""
+    _check(load().snn_debug_offset_count(handle, int(column), int(delta), 1 if group_only else 0),
+           handle)
 
 
 def snn_step_profiled(handle, n_steps):

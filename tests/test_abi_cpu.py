@@ -164,6 +164,8 @@ def test_noalloc_update_validates_before_touching_a_device(lib):
     assert call(spikes=None) == snn.SNN_EINVAL
     assert call(v=p + 4) == snn.SNN_EINVAL  # V must be 16-byte aligned
     assert call(refractory=p + 2) == snn.SNN_EINVAL  # refractory must be 4-byte aligned
+    assert call(spikes=p + 2) == snn.SNN_EINVAL  # spike ids are stored as u32
+    assert call(col_counts=p + 4) == snn.SNN_EINVAL  # u64 counters
 
 
 def test_spike_readback_refuses_unsafe_output_arrays(lib):

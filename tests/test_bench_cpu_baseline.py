@@ -83,3 +83,22 @@ def test_clock_records_that_disqualify_a_timing():
         assert bench.clocks_rejected(dict(ok, reasons=[r]))
     assert bench.clocks_rejected(dict(ok, sm_mhz=1200.0))  # locked low, no reason
     assert not bench.any_rank(None, False, "cpu") and bench.any_rank(None, True, "cpu")
+
+
+def test_reference_arm_line_on_a_tiny_workload(orc, capsys):
+    """The reference arm times the oracle for exactly K steps after W warm-up
+    steps and prints the same config object as the GPU arm."""
+    import argparse
+    import json
+
+    import bench
+    from paper_1511_09325_gb300 import workloads as W
+
+    args = argparse.Namespace(workload="cols2x2_f32w", steps=4, warmup=2, gpus=1, settle=0)
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 4 and line["warmup"] == 2
+    assert line["value"] > 0 and line["unit"] == bench.UNIT
+    assert line["config"] == bench._config(args, W.WORKLOADS["cols2x2_f32w"], None, 1)
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert "steps 2..5" in line["cpu_baseline"]["sample"]

@@ -210,31 +210,66 @@ def test_full_size_24x24_f32w():
     assert np.array_equal(v.astype(np.float64), o["v"])
 
 
-def test_full_size_96x96_f16w():
-    """The 96x96 workload (11.43 M neurons, 14.17 G synapses, FP16 weights):
-    sampled rows of the table, and the first step of sampled neurons
-    (no recurrent input yet) against the oracle's neuron update."""
-    cfg = W.WORKLOADS["cols96x96_f16w"]
+@pytest.fixture(scope="module")
+def full_size_oracle():
+    """The oracle's 3-step runs of the 96x96 F16W and 48x48 F32W workloads,
+    started in parallel processes when the first full-size test asks for
+    them (each takes minutes on one core)."""
+    from oracle_pool import OraclePool
+
     n, s = W.neuron_params(), W.synapse_params()
-    p = oracle.make_params(96, 96, n, s, cfg["seed"])
-    with snn.Net(96, 96, n, s, cfg["seed"], "f16w") as net:
-        assert net.info()["synapses"] == 14170521600
-        rng = np.random.default_rng(2)
-        for j0 in rng.choice(net.n - 4, 8, replace=False):
-            _compare_rows(net, p, "f16w", int(j0), 4)
-        _compare_rows(net, p, "f16w", net.n - 4, 4)
-        net.step(1)
-        v, _, r = net.state()
-        st, ids, _ = net.spikes()
-    fired = set(ids.tolist())
-    blocks = [0, (net.n // 2) - 1000, net.n - 1240]
-    for j0 in blocks:
-        v0 = oracle.init_v(p, "f32w", j0, 1240)
-        k = oracle.ext_counts(p, j0, 1240, 0)
-        for e in range(1240):
-            i = j0 + e
-            pop = 0 if i % 1240 < 992 else 1
-            vo, _, so = oracle.neuron_trace(p, "f32w", pop, v0[e], 0.0,
-                                            np.array([int(k[e]) * 26214], np.int32))
-            assert v[i] == vo[0]
-            assert (i in fired) == bool(so[0])
+    pool = OraclePool(workers=2)
+    jobs = {}
+    for name, gw, prec in (("cols96x96_f16w", 96, "f16w"), ("cols48x48_f32w", 48, "f32w")):
+        N = gw * gw * n["n_per_col"]
+        jobs[name] = pool.submit((gw, gw), n, s, W.WORKLOADS[name]["seed"], prec, 3, N)
+    yield jobs
+    pool.close()
+
+
+def _full_size_steps(name, rows_seed, job):
+    """Build the workload in the benchmark's launch configuration, compare
+    sampled rows of the table, run 3 steps, and compare the whole raster and
+    the whole final state with the oracle's."""
+    cfg = W.WORKLOADS[name]
+    gw, prec, seed = cfg["grid_w"], cfg["precision"], cfg["seed"]
+    n, s = W.neuron_params(), W.synapse_params()
+    p = oracle.make_params(gw, gw, n, s, seed)
+    with snn.Net(gw, gw, n, s, seed, prec) as net:
+        N = net.n
+        assert net.info()["synapses"] == N * 1240
+        rng = np.random.default_rng(rows_seed)
+        for j0 in rng.choice(N - 4, 6, replace=False):
+            _compare_rows(net, p, prec, int(j0), 4)
+        _compare_rows(net, p, prec, N - 4, 4)
+        net.set_record_capacity(N)
+        net.step(3)
+        st, ids, over = net.spikes()
+        v, c, r = net.state()
+        rec, _, done = net.stats()
+    o = job.get()
+    assert not over and done == 3
+    assert np.array_equal(_sorted_raster(st, ids), o["key"])
+    assert rec == len(o["key"]) * 1240
+    assert np.array_equal(v.astype(np.float64), o["v"])
+    assert np.array_equal(c.astype(np.float64), o["c"])
+    assert np.array_equal(r, o["r"])
+    return o
+
+
+def test_full_size_96x96_f16w_three_steps(full_size_oracle):
+    """The 96x96 workload (11.43 M neurons, 14.17 G synapses, FP16 weights,
+    seed 3): the whole raster and every neuron's state after 3 steps equal
+    the oracle's.  Rows j >= 2^32 / row capacity (~3.1 M) start beyond slot
+    2^32 of the table, so the deliveries of steps 0 and 1 (delays 1 and 2)
+    run through the 64-bit slot arithmetic on most spikers."""
+    o = _full_size_steps("cols96x96_f16w", 2, full_size_oracle["cols96x96_f16w"])
+    assert o["step_spikes"][0] > 100000 and o["step_spikes"][2] > 0
+    assert o["i_max"] > (1 << 32) // 1384
+
+
+def test_full_size_48x48_f32w_three_steps(full_size_oracle):
+    """The 48x48 FP32-weight comparison network (2.86 M neurons, 3.54 G
+    synapses, seed 3): whole raster and state after 3 steps."""
+    o = _full_size_steps("cols48x48_f32w", 3, full_size_oracle["cols48x48_f32w"])
+    assert o["step_spikes"][0] > 10000
