@@ -20,6 +20,8 @@ struct snn_net {
   bool agg = true;
   int deliver_grid = 0;
   int tile = 1, ring = 1, win_cap = 0, desc_words = 8;  // delivery tiles and windows
+  size_t window_budget = 0;  // bytes of shared memory a delivery window may take
+  unsigned min_items = 256;  // fewest items a delivery block takes
   long long N = 0, Npad = 0, ncol = 0;
   uint64_t seed = 0;
   snn_neuron_params neuron{};
@@ -206,8 +208,15 @@ uint32_t recip32(uint32_t d) {
 
 // Delivery tiles: the largest square tile (side <= kMaxTile) whose window --
 // the tile plus a ring of one column, clipped to the grid -- fits the shared
-// memory budget of a delivery block.
+// memory budget of a delivery block: one block per SM for a net of its own,
+// two per SM in the batch kernel.
 constexpr size_t kWindowBudget = 196 * 1024;
+constexpr size_t kBatchWindowBudget = 96 * 1024;
+// Fewest items a delivery block takes (fewer blocks run when a step has few
+// items).  Measured on the 64-net batch: 256 per block beat 512, 2048 and
+// 8192, so members use the same value as nets of their own.
+constexpr unsigned kMinItems = 256;
+constexpr unsigned kBatchMinItems = 256;
 
 void choose_tiles(snn_net* net) {
   net->ring = 1;
@@ -215,7 +224,7 @@ void choose_tiles(snn_net* net) {
   for (; t > 1; --t) {
     const size_t ww = (size_t)std::min(t + 2 * net->ring, net->W);
     const size_t wh = (size_t)std::min(t + 2 * net->ring, net->H);
-    if (ww * wh * (size_t)net->npc * 4 <= kWindowBudget) break;
+    if (ww * wh * (size_t)net->npc * 4 <= net->window_budget) break;
   }
   net->tile = t;
   const long long ww = std::min(t + 2 * net->ring, net->W);
@@ -288,6 +297,7 @@ void fill_step_params(snn_net* net) {
   p.ring = net->ring;
   p.win_cap = net->win_cap;
   p.desc_words = net->desc_words;
+  p.min_items = net->min_items;
   p.npc_m = recip32((uint32_t)net->npc);
   p.w_m = recip32((uint32_t)net->W);
   p.seed_lo = (uint32_t)(net->seed & 0xFFFFFFFFu);
@@ -529,9 +539,13 @@ int net_view(snn_net* net, NetView* v) {
 
 extern "C" {
 
-int snn_build(int grid_w, int grid_h, const snn_neuron_params* neuron,
+}  // extern "C"
+
+namespace {
+
+int build_net(int grid_w, int grid_h, const snn_neuron_params* neuron,
               const snn_synapse_params* synapse, uint64_t seed, int precision,
-              void* cuda_stream, snn_net** out) {
+              void* cuda_stream, size_t window_budget, unsigned min_items, snn_net** out) {
   if (!out) return fail(nullptr, SNN_EINVAL, "out is NULL");
   *out = nullptr;
   std::string why;
@@ -539,6 +553,8 @@ int snn_build(int grid_w, int grid_h, const snn_neuron_params* neuron,
   if (vrc != SNN_OK) return fail(nullptr, vrc, why);
   snn_net* net = new (std::nothrow) snn_net();
   if (!net) return fail(nullptr, SNN_ENOMEM, "host allocation failed");
+  net->window_budget = window_budget;
+  net->min_items = min_items;
   if (cuda_stream) {
     net->stream = static_cast<cudaStream_t>(cuda_stream);
   } else {
@@ -558,6 +574,17 @@ int snn_build(int grid_w, int grid_h, const snn_neuron_params* neuron,
   }
   *out = net;
   return SNN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int snn_build(int grid_w, int grid_h, const snn_neuron_params* neuron,
+              const snn_synapse_params* synapse, uint64_t seed, int precision,
+              void* cuda_stream, snn_net** out) {
+  return build_net(grid_w, grid_h, neuron, synapse, seed, precision, cuda_stream, kWindowBudget,
+                   kMinItems, out);
 }
 
 int snn_step(snn_net* net, int64_t n_steps) {
@@ -1105,8 +1132,8 @@ int snn_batch_build(int n_nets, const int32_t* grid_w, const int32_t* grid_h,
   b->first.assign(2 * (size_t)(n_nets + 1), 0);
   for (int k = 0; k < n_nets && rc == SNN_OK; ++k) {
     snn_net* net = nullptr;
-    rc = snn_build(grid_w[k], grid_h[k], neuron + k, synapse + k, seeds[k], precision, b->stream,
-                   &net);
+    rc = build_net(grid_w[k], grid_h[k], neuron + k, synapse + k, seeds[k], precision, b->stream,
+                   kBatchWindowBudget, kBatchMinItems, &net);
     if (rc != SNN_OK) break;
     net->in_batch = true;
     b->nets.push_back(net);

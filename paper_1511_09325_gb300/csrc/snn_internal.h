@@ -122,6 +122,7 @@ struct StepParams {
   int tile, ring;          // delivery tile side and window ring, in columns
   int win_cap;             // ints of the window (largest tile window)
   int desc_words;          // u32 words per spike descriptor (8 or 16)
+  unsigned min_items;      // fewest items a delivery block takes (fewer blocks run)
   uint32_t npc_m, w_m;     // floor(2^32 / n_per_col), floor(2^32 / W) (capped)
   uint32_t seed_lo, seed_hi;
   float theta, vr, dc, pvv, pcc, pvc_e, pvc_i;

@@ -41,15 +41,14 @@ namespace {
 
 constexpr int kUpdateThreads = 256;
 constexpr int kDeliverThreads = 1024;  // one delivery block per SM
-constexpr int kBatchThreads = 1024;    // batch kernel: 4 update sub-blocks or one delivery block
+constexpr int kBatchThreads = 512;     // batch kernel: 2 update sub-blocks or one delivery block
 constexpr int kUpdateSubs = kBatchThreads / kUpdateThreads;
 constexpr int kInflightF32 = 1;  // 32-byte sectors per lane and stage, F32W (2 loads each)
 constexpr int kInflightF16 = 2;  // the same for F16W (two stages in flight)
 constexpr int kTile = kUpdateThreads * 4;    // neurons per update tile
 constexpr int kTileCols = kTile / 2 + 2;     // columns a tile can touch (npc >= 2)
 constexpr int kBatchItems = 32;              // items per warp batch (one per lane)
-constexpr unsigned kMinItems = 256;          // fewest items a delivery block takes
-constexpr unsigned kWinMinItems = 1024;      // fewest items of a tile part that uses the window
+constexpr unsigned kWinMinItems = 512;       // fewest items of a tile part that uses the window
 
 struct NeuronOut {
   float v, c;
@@ -642,7 +641,7 @@ __device__ __forceinline__ void stream_items(const StepParams& P, const Item& it
 
 // Delivery block vb of vgrid (NT threads) for step t.  The step's items,
 // ordered by (virtual column, delay bucket, spiker), are split into at most
-// vgrid equal contiguous ranges of at least kMinItems items; block vb
+// vgrid equal contiguous ranges of at least P.min_items items; block vb
 // locates the first and last virtual column of its range from the group and
 // column counts (gsum, isum) and walks the tiles it meets.  For each tile
 // part it tabulates the (column, bucket) counts, builds the F16W neighbour
@@ -685,7 +684,7 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
   for (int g = g0; g < g0 + per && g < ngrp; ++g) mine += P.gsum[g];
   unsigned long long total = 0ull;
   const unsigned long long excl = block_scan(mine, S, &total);
-  const unsigned long long want = (total + kMinItems - 1) / kMinItems;
+  const unsigned long long want = (total + P.min_items - 1) / P.min_items;
   const int nact = (int)(want < (unsigned long long)vgrid ? (want ? want : 1ull) : (unsigned long long)vgrid);
   if (vb >= nact) return;
   const unsigned long long lo = total * (unsigned long long)vb / (unsigned long long)nact;
@@ -887,7 +886,7 @@ __global__ void __launch_bounds__(kDeliverThreads, 1) deliver_kernel(const StepP
 
 // ---------------------------------------------------------------------------
 // Batched form: many independent nets advanced by one persistent launch.
-// Every step runs the update bodies of all nets (four 256-thread sub-blocks
+// Every step runs the update bodies of all nets (two 256-thread sub-blocks
 // per block, each with its own named barrier), a grid barrier, the delivery
 // bodies of all nets (whole blocks), and a second barrier.  Virtual body g of
 // a phase belongs to net k with first[k] <= g < first[k + 1]; each virtual
@@ -951,7 +950,7 @@ __device__ __forceinline__ int net_of(const int* first, int n, int g) {
 }
 
 template <int PREC, int INFL>
-__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(const BatchParams B) {
+__global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchParams B) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ StepParams s_p[kUpdateSubs];  // the nets of the current virtual bodies
   __shared__ DeliverSmem SD;
