@@ -20,6 +20,7 @@ struct snn_net {
   bool agg = true;
   int deliver_grid = 0;
   int tile = 1, ring = 1, win_cap = 0, desc_words = 8;  // delivery tiles and windows
+  int part_cols = kMaxTileCols;
   size_t window_budget = 0;  // bytes of shared memory a delivery window may take
   unsigned min_items = 256;  // fewest items a delivery block takes
   long long N = 0, Npad = 0, ncol = 0;
@@ -217,6 +218,11 @@ constexpr size_t kBatchWindowBudget = 96 * 1024;
 // 8192, so members use the same value as nets of their own.
 constexpr unsigned kMinItems = 256;
 constexpr unsigned kBatchMinItems = 256;
+// Most columns of a delivery part without window (runs of sparse tiles): its
+// (column, bucket) and neighbour tables take part_cols * (d_max + 64) words
+// of shared memory beside the window.
+constexpr int kPartCols = kMaxTileCols;
+constexpr int kBatchPartCols = 16;
 
 void choose_tiles(snn_net* net) {
   net->ring = 1;
@@ -227,6 +233,7 @@ void choose_tiles(snn_net* net) {
     if (ww * wh * (size_t)net->npc * 4 <= net->window_budget) break;
   }
   net->tile = t;
+  net->part_cols = std::max(net->part_cols, t * t);
   const long long ww = std::min(t + 2 * net->ring, net->W);
   const long long wh = std::min(t + 2 * net->ring, net->H);
   net->win_cap = (int)((ww * wh * net->npc + 3) / 4 * 4);
@@ -294,6 +301,7 @@ void fill_step_params(snn_net* net) {
   p.ncol = (int)net->ncol;
   p.agg = net->agg ? 1 : 0;
   p.tile = net->tile;
+  p.part_cols = net->part_cols;
   p.ring = net->ring;
   p.win_cap = net->win_cap;
   p.desc_words = net->desc_words;
@@ -545,7 +553,8 @@ namespace {
 
 int build_net(int grid_w, int grid_h, const snn_neuron_params* neuron,
               const snn_synapse_params* synapse, uint64_t seed, int precision,
-              void* cuda_stream, size_t window_budget, unsigned min_items, snn_net** out) {
+              void* cuda_stream, size_t window_budget, unsigned min_items, int part_cols,
+              snn_net** out) {
   if (!out) return fail(nullptr, SNN_EINVAL, "out is NULL");
   *out = nullptr;
   std::string why;
@@ -555,6 +564,7 @@ int build_net(int grid_w, int grid_h, const snn_neuron_params* neuron,
   if (!net) return fail(nullptr, SNN_ENOMEM, "host allocation failed");
   net->window_budget = window_budget;
   net->min_items = min_items;
+  net->part_cols = part_cols;
   if (cuda_stream) {
     net->stream = static_cast<cudaStream_t>(cuda_stream);
   } else {
@@ -584,7 +594,7 @@ int snn_build(int grid_w, int grid_h, const snn_neuron_params* neuron,
               const snn_synapse_params* synapse, uint64_t seed, int precision,
               void* cuda_stream, snn_net** out) {
   return build_net(grid_w, grid_h, neuron, synapse, seed, precision, cuda_stream, kWindowBudget,
-                   kMinItems, out);
+                   kMinItems, kPartCols, out);
 }
 
 int snn_step(snn_net* net, int64_t n_steps) {
@@ -1133,7 +1143,7 @@ int snn_batch_build(int n_nets, const int32_t* grid_w, const int32_t* grid_h,
   for (int k = 0; k < n_nets && rc == SNN_OK; ++k) {
     snn_net* net = nullptr;
     rc = build_net(grid_w[k], grid_h[k], neuron + k, synapse + k, seeds[k], precision, b->stream,
-                   kBatchWindowBudget, kBatchMinItems, &net);
+                   kBatchWindowBudget, kBatchMinItems, kBatchPartCols, &net);
     if (rc != SNN_OK) break;
     net->in_batch = true;
     b->nets.push_back(net);

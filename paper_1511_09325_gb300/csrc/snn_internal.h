@@ -120,6 +120,7 @@ struct StepParams {
   int ncol;
   int agg;  // shared-memory windows over each delivery tile and its ring
   int tile, ring;          // delivery tile side and window ring, in columns
+  int part_cols;           // most columns of a delivery part without window (>= tile^2)
   int win_cap;             // ints of the window (largest tile window)
   int desc_words;          // u32 words per spike descriptor (8 or 16)
   unsigned min_items;      // fewest items a delivery block takes (fewer blocks run)

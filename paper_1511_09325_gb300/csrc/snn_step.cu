@@ -33,6 +33,8 @@
 //   double-buffered in registers; the next batch is resolved before the
 //   current one is streamed.  Integer addition makes the result independent
 //   of the order.  The last block to finish advances the step counter.
+#include <algorithm>
+
 #include "snn_device.cuh"
 #include "snn_internal.h"
 
@@ -436,20 +438,25 @@ struct DeliverSmem {
   int xg[2];                      // group holding lo / hi - 1
   int v0, v1;                     // first and last virtual column of the block's items
   int slot[kMaxDelays];           // slot of each bucket's step, -1 before step 0
+  int pe;                         // end (exclusive) of the current part
+  int pwin;                       // the current part uses the window
   int ccol[kMaxTileCols];         // real column of each column of the current tile part
   int cx[kMaxTileCols], cy[kMaxTileCols];  // its grid position
   uint32_t wbase[(kMaxTile + 2) * (kMaxTile + 2)];  // first neuron of each window slot's column
   unsigned next;                  // next batch of the current tile part
 };
 
-// Words of the (column, bucket) table and of the F16W neighbour table in the
-// dynamic shared memory of a delivery block; the window follows them.
-__device__ __forceinline__ int tab_words(const StepParams& P) {
-  return (P.tile * P.tile * P.ndel + 1 + 3) & ~3;
+// Words of the (column, bucket) table and of the F16W neighbour table of a
+// part of `cols` columns.  In the dynamic shared memory of a delivery block
+// the tables of a windowed part (one tile, at most tile^2 columns) come first,
+// then the window; a part without window (at most part_cols columns) keeps
+// its tables at the start of the window area, which it does not use.
+__device__ __forceinline__ int tab_words(const StepParams& P, int cols) {
+  return (cols * P.ndel + 1 + 3) & ~3;
 }
 template <int PREC>
-__device__ __forceinline__ int nb_words(const StepParams& P) {
-  return PREC == SNN_EXACT_F16W ? P.tile * P.tile * 64 : 0;
+__device__ __forceinline__ int nb_words(int cols) {
+  return PREC == SNN_EXACT_F16W ? cols * 64 : 0;
 }
 
 // Block-wide exclusive scan of one 64-bit value per thread; *total gets the
@@ -656,9 +663,11 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  unsigned* tab = reinterpret_cast<unsigned*>(dyn);
-  uint32_t* nb = tab + tab_words(P);
-  int32_t* win = reinterpret_cast<int32_t*>(nb + nb_words<PREC>(P));
+  unsigned* const tab_w = reinterpret_cast<unsigned*>(dyn);  // windowed parts
+  uint32_t* const nb_w = tab_w + tab_words(P, P.tile * P.tile);
+  int32_t* const win = reinterpret_cast<int32_t*>(nb_w + nb_words<PREC>(P.tile * P.tile));
+  unsigned* const tab_s = reinterpret_cast<unsigned*>(win);  // parts without window
+  uint32_t* const nb_s_ = tab_s + tab_words(P, P.part_cols);
   // the slot that the next update fills holds step t - d_max: no longer read
   const long long next_slot = (t + 1) % P.nslot;
   if (vb == 0 && tid == 0) P.cnt[next_slot] = 0u;
@@ -736,13 +745,51 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
 
   const uint64_t pol = evict_last_policy();
   const uint32_t win_s = (uint32_t)__cvta_generic_to_shared(win);
-  const uint32_t nb_s = (uint32_t)__cvta_generic_to_shared(nb);
   unsigned long long pbase = S.p0;  // items before the tile part's first column
   unsigned long long covered = 0ull;  // items of the range found in the spike lists
   bool win_zero = false;              // the window has been cleared in this body
   for (int v = v0; v <= v1;) {
+    // the part's extent: one tile whose items in the range reach the window
+    // threshold (delivered through the window), else a run of consecutive
+    // tiles below it, at most P.part_cols columns (delivered without one)
+    if (warp == 0) {
+      int e = v, tiles = 0;
+      bool wnd = false;
+      unsigned long long pb = pbase;  // items before column e
+      while (e <= v1) {
+        const TileGeo gt = tile_geo(P, e);
+        const int te = min(v1, gt.first + gt.tw * gt.th - 1);
+        if (tiles > 0 && te - v + 1 > P.part_cols) break;
+        unsigned x = 0u;
+        for (int c = e + lane; c <= te; c += 32) x += P.isum[c];
+        x = __reduce_add_sync(0xFFFFFFFFu, x);
+        const unsigned long long lo_in = pb > lo ? pb : lo;
+        const unsigned long long hi_in = pb + x < hi ? pb + x : hi;
+        const unsigned long long in = hi_in > lo_in ? hi_in - lo_in : 0ull;
+        if (P.agg && in >= kWinMinItems) {
+          if (tiles == 0) {
+            wnd = true;
+            e = te + 1;
+          }
+          break;
+        }
+        pb += x;
+        e = te + 1;
+        ++tiles;
+      }
+      if (lane == 0) {
+        S.pe = e;
+        S.pwin = wnd ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    const int ve = S.pe - 1;
+    const bool windowed = S.pwin != 0;
+    unsigned* const tab = windowed ? tab_w : tab_s;
+    uint32_t* const nb = windowed ? nb_w : nb_s_;
+    const uint32_t nb_s = (uint32_t)__cvta_generic_to_shared(nb);
+    if (!windowed) win_zero = false;  // the tables overwrite the window area
     const TileGeo g = tile_geo(P, v);
-    const int ve = min(v1, g.first + g.tw * g.th - 1);
     const int ncv = ve - v + 1;
     const int n_entries = ncv * P.ndel;
     for (int k = tid; k < ncv; k += NT) {
@@ -785,7 +832,6 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
     const unsigned a = lo > pbase ? (unsigned)(lo - pbase) : 0u;
     const unsigned b = hi > pbase ? (unsigned)min(hi - pbase, ptotal) : 0u;
     covered += b > a ? b - a : 0u;
-    const bool windowed = P.agg && b > a && b - a >= kWinMinItems;
     const WinGeo wg = win_geo(P, g, windowed);
     if (windowed && !win_zero) {
       for (int i = tid; i < (P.win_cap >> 2); i += NT) reinterpret_cast<int4*>(win)[i] = make_int4(0, 0, 0, 0);
@@ -1116,9 +1162,14 @@ cudaError_t launch_update(const StepParams& p, int grid, cudaStream_t st) {
 }
 
 size_t deliver_smem(const StepParams& p, int precision) {
-  const size_t tabw = ((size_t)p.tile * p.tile * p.ndel + 1 + 3) & ~(size_t)3;
-  const size_t nbw = precision == SNN_EXACT_F16W ? (size_t)p.tile * p.tile * 64 : 0;
-  return (tabw + nbw + (size_t)p.win_cap) * 4;
+  auto tables = [&](size_t cols) {
+    const size_t tabw = (cols * (size_t)p.ndel + 1 + 3) & ~(size_t)3;
+    return tabw + (precision == SNN_EXACT_F16W ? cols * 64 : 0);
+  };
+  // windowed-part tables, then the window area (which also holds the tables
+  // of a part without window)
+  const size_t area = std::max((size_t)p.win_cap, tables((size_t)p.part_cols));
+  return (tables((size_t)p.tile * p.tile) + area) * 4;
 }
 
 int deliver_threads() { return kDeliverThreads; }
