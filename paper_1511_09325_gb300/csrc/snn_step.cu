@@ -105,42 +105,6 @@ __device__ __forceinline__ void red_add(int32_t* p, int32_t v, uint64_t pol) {
                : "memory");
 }
 
-// The same, issued only where `on` is nonzero: a predicated instruction, so
-// lanes that take different paths do not split the warp.
-__device__ __forceinline__ void red_add_if(uint32_t on, int32_t* p, int32_t v, uint64_t pol) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
-      "@q red.global.add.L2::cache_hint.s32 [%1], %2, %3;\n\t}" ::"r"(on),
-      "l"(p), "r"(v), "l"(pol)
-      : "memory");
-}
-
-// The two predicated reductions of the record path, without a compiler
-// memory barrier: nothing the delivery loop reads aliases the window or the
-// accumulator (both are read only after the block's next barrier), so the
-// compiler may move loads of the synapse table across them.
-__device__ __forceinline__ void red_add_if_nb(uint32_t on, int32_t* p, int32_t v, uint64_t pol) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
-      "@q red.global.add.L2::cache_hint.s32 [%1], %2, %3;\n\t}" ::"r"(on),
-      "l"(p), "r"(v), "l"(pol));
-}
-__device__ __forceinline__ void red_shared_if_nb(uint32_t on, uint32_t a, int32_t v) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
-      "@q red.shared.add.s32 [%1], %2;\n\t}" ::"r"(on),
-      "r"(a), "r"(v));
-}
-
-// Predicated int32 reduction into shared memory (shared-window address `a`).
-__device__ __forceinline__ void red_shared_if(uint32_t on, uint32_t a, int32_t v) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
-      "@q red.shared.add.s32 [%1], %2;\n\t}" ::"r"(on),
-      "r"(a), "r"(v)
-      : "memory");
-}
-
 // Loads of the neuron state, read once per step: no L1 allocation, so that
 // L1 capacity does not bound the loads a block keeps in flight.
 __device__ __forceinline__ float4 ld_stream(const float4* p) {
@@ -484,40 +448,53 @@ __device__ __forceinline__ unsigned long long block_scan(unsigned long long v, D
   return before + incl - v;
 }
 
-// rint(x) for |x| < 2^22 by one rounded addition: x + 1.5 * 2^23 lands in
-// [2^23, 2^24), where the float grid is the integers, so the addition rounds
-// x to the nearest integer (ties to even) and the low mantissa bits hold it.
-constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
-constexpr int32_t kRoundMagicBits = 0x4B400000;
-
-// Deliver one synapse of weight wfx (2^-16 mV units) to the shared-window
-// address `sa` (inwin) or to the accumulator at byte offset `gofs`; zero
-// weights (padding records, unused slots) deliver nothing.  Both reductions
-// are predicated, so the warp never diverges here.
-__device__ __forceinline__ void deliver_to(int32_t wfx, bool inwin, uint32_t sa, uint32_t gofs,
-                                           const StepParams& P, uint64_t pol) {
-  const uint32_t on = wfx != 0 ? 1u : 0u;
-  red_shared_if_nb(on & (inwin ? 1u : 0u), sa, wfx);
-  red_add_if_nb(on & (inwin ? 0u : 1u),
-                reinterpret_cast<int32_t*>(reinterpret_cast<char*>(P.acc) + gofs), wfx, pol);
-}
-
-// F16W record w = half_magnitude(15) << 17 | offset(6) << 11 | l(11): the
-// offset picks, in the neighbour-table row `nbrow` of the spiker's column, the
-// target column -- its shared window address, or bit 31 set and its first
-// neuron in the accumulator.
+// One F16W record w = half_magnitude(15) << 17 | offset(6) << 11 | l(11),
+// as one PTX block: the offset picks, in the neighbour-table row `nbrow` of
+// the spiker's column, the target column -- its shared-window address, or
+// bit 31 set and its first neuron in the accumulator; the weight
+// rint(half * 2^16) comes from one rounded multiply-add (x * (+-2^16) +
+// 1.5 * 2^23 lands in [2^23, 2^24), where the float grid is the integers, so
+// the low mantissa bits hold the rounded product); one setp gives both
+// predicates, and zero weights (padding records, unused lanes) deliver
+// nothing.  No compiler memory barrier: nothing this loop reads aliases the
+// window or the accumulator.
 __device__ __forceinline__ void deliver_f16(uint32_t w, uint32_t nbrow, float wsign,
-                                            const StepParams& P, uint64_t pol) {
-  uint32_t e;
-  asm("ld.shared.u32 %0, [%1];" : "=r"(e) : "r"(nbrow + ((w >> 9) & 0xFCu)));
-  const uint32_t l4 = (w << 2) & 0x1FFCu;
-  const float hf = __half2float(__ushort_as_half((unsigned short)(w >> 17)));
-  const int32_t wfx = __float_as_int(__fmaf_rn(hf, wsign, kRoundMagic)) - kRoundMagicBits;
-  deliver_to(wfx, (int)e >= 0, e + l4, (e << 2) + l4, P, pol);
+                                            const int32_t* acc, uint64_t pol) {
+  asm volatile(
+      "{\n\t"
+      ".reg .u32 t, e, l4, sa, go;\n\t"
+      ".reg .b16 h, hh;\n\t"
+      ".reg .f32 hf, x;\n\t"
+      ".reg .s32 wfx;\n\t"
+      ".reg .u64 ga;\n\t"
+      ".reg .pred pon, pg, ps;\n\t"
+      "shr.b32 t, %0, 9;\n\t"
+      "and.b32 t, t, 252;\n\t"
+      "add.u32 t, t, %1;\n\t"
+      "ld.shared.u32 e, [t];\n\t"
+      "shl.b32 l4, %0, 2;\n\t"
+      "and.b32 l4, l4, 8188;\n\t"
+      "shr.b32 t, %0, 17;\n\t"
+      "mov.b32 {h, hh}, t;\n\t"
+      "cvt.f32.f16 hf, h;\n\t"
+      "fma.rn.f32 x, hf, %2, 0f4B400000;\n\t"
+      "mov.b32 wfx, x;\n\t"
+      "sub.s32 wfx, wfx, 1262485504;\n\t"
+      "setp.ne.s32 pon, wfx, 0;\n\t"
+      "setp.lt.and.s32 pg|ps, e, 0, pon;\n\t"
+      "add.u32 sa, e, l4;\n\t"
+      "@ps red.shared.add.s32 [sa], wfx;\n\t"
+      "shl.b32 go, e, 2;\n\t"
+      "add.u32 go, go, l4;\n\t"
+      "cvt.u64.u32 ga, go;\n\t"
+      "add.u64 ga, ga, %3;\n\t"
+      "@pg red.global.add.L2::cache_hint.s32 [ga], wfx, %4;\n\t"
+      "}" ::"r"(w),
+      "r"(nbrow), "f"(wsign), "l"(acc), "l"(pol));
 }
 
 // F32W record {target neuron, round(w * 2^16)}: the target's column is tested
-// against the tile's window.
+// against the tile's window; then one setp gives both predicates as above.
 __device__ __forceinline__ void deliver_f32(uint32_t t, int32_t wfx, const WinGeo& wg,
                                             uint32_t win_s, const StepParams& P, uint64_t pol) {
   const uint32_t col = div_by(t, (uint32_t)P.npc, P.npc_m);
@@ -528,9 +505,16 @@ __device__ __forceinline__ void deliver_f32(uint32_t t, int32_t wfx, const WinGe
   rx += rx < 0 ? P.W : 0;
   int ry = (int)y - wg.y0;
   ry += ry < 0 ? P.H : 0;
-  const bool inwin = (unsigned)rx < (unsigned)wg.ww && (unsigned)ry < (unsigned)wg.wh;
-  const uint32_t wt = ((uint32_t)ry * (uint32_t)wg.ww + (uint32_t)rx) * (uint32_t)P.npc + l;
-  deliver_to(wfx, inwin, win_s + 4u * wt, t << 2, P, pol);
+  const uint32_t inwin = ((unsigned)rx < (unsigned)wg.ww && (unsigned)ry < (unsigned)wg.wh) ? 1u : 0u;
+  const uint32_t sa = win_s + 4u * (((uint32_t)ry * (uint32_t)wg.ww + (uint32_t)rx) * (uint32_t)P.npc + l);
+  const int32_t* ga = P.acc + t;
+  asm volatile(
+      "{\n\t.reg .pred pon, pg, ps;\n\t"
+      "setp.ne.s32 pon, %2, 0;\n\t"
+      "setp.eq.and.u32 ps|pg, %3, 1, pon;\n\t"
+      "@ps red.shared.add.s32 [%0], %2;\n\t"
+      "@pg red.global.add.L2::cache_hint.s32 [%1], %2, %4;\n\t}" ::"r"(sa),
+      "l"(ga), "r"(wfx), "r"(inwin), "l"(pol));
 }
 
 // A resolved item: the bucket a lane streams.
@@ -591,58 +575,89 @@ __device__ __forceinline__ Item resolve_item(const StepParams& P, unsigned item,
   return it;
 }
 
-// One warp streams its lanes' items, each lane its own bucket, a 32-byte
-// sector of records (F16W: 8 synapses; F32W: 4) per unit, INFL units in
-// flight.
-template <int PREC, int INFL>
+// One warp streams the buckets of its lanes' items as one list of 32-byte
+// sectors (F16W: 8 records; F32W: 4), dealt to the lanes in rounds of 32, so
+// no lane idles while another finishes a longer bucket.  The sector of lane L
+// in round g0 belongs to the item holding g0 plus the items that start
+// between g0 and g0 + L (a ballot and an or-reduction over the items' first
+// sectors); the item's fields come by shuffle.  The next round's sectors are
+// requested before the current ones are delivered.
+template <int PREC>
 __device__ __forceinline__ void stream_items(const StepParams& P, const Item& it, uint32_t win_s,
                                              const WinGeo& wg, uint64_t pol) {
-  const int units = it.units;
-  const uint32_t nbrow = it.nbrow;
-  const float wsign = it.wsign;
-  const int umax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)units);
-  // double buffer: the next INFL sectors are requested before the current
-  // ones are delivered (unused sectors read as weight 0)
-  uint4 cur[INFL][2], nxt[INFL][2];
+  const int lane = threadIdx.x & 31;
+  // compact the non-empty items to lanes 0 .. nit - 1
+  const unsigned cm = __ballot_sync(0xFFFFFFFFu, it.units > 0);
+  const int nit = __popc(cm);
+  if (nit == 0) return;
+  const int src = lane < nit ? (int)__fns(cm, 0u, lane + 1) : 0;
+  const unsigned long long sp = reinterpret_cast<unsigned long long>(it.src);
+  int units = __shfl_sync(0xFFFFFFFFu, it.units, src);
+  const unsigned slo = __shfl_sync(0xFFFFFFFFu, (unsigned)sp, src);
+  const unsigned shi = __shfl_sync(0xFFFFFFFFu, (unsigned)(sp >> 32), src);
+  const uint32_t nbr = __shfl_sync(0xFFFFFFFFu, it.nbrow, src);
+  const float wsg = __shfl_sync(0xFFFFFFFFu, it.wsign, src);
+  const bool mine = lane < nit;
+  if (!mine) units = 0;
+  int incl = units;
 #pragma unroll
-  for (int u = 0; u < INFL; ++u) {
-    cur[u][0] = cur[u][1] = make_uint4(0u, 0u, 0u, 0u);
-    if (u < units) {
-      cur[u][0] = __ldcs(it.src + 2 * u);
-      cur[u][1] = __ldcs(it.src + 2 * u + 1);
-    }
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += v;
   }
-  for (int u0 = 0; u0 < umax; u0 += INFL) {
+  const int pre = incl - units;  // first sector of compact item `lane`
+  const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  const unsigned le_mask = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+  const int32_t* acc = P.acc;
+
+  // sector of round g0 for this lane: its two 16-byte halves and its item's fields
+  auto fetch = [&](int g0, uint4& r0, uint4& r1, uint32_t& nbrow, float& wsign) {
+    r0 = r1 = make_uint4(0u, 0u, 0u, 0u);  // weight 0: nothing delivered
+    nbrow = 0u;
+    wsign = 65536.0f;
+    if (g0 >= total) return;
+    const int ebase = __popc(__ballot_sync(0xFFFFFFFFu, mine && pre <= g0)) - 1;
+    const int pos = pre - g0;
+    const unsigned bit = (mine && pos > 0 && pos < 32) ? (1u << pos) : 0u;
+    const unsigned starts = __reduce_or_sync(0xFFFFFFFFu, bit);
+    const int e = ebase + __popc(starts & le_mask);
+    const unsigned lo = __shfl_sync(0xFFFFFFFFu, slo, e);
+    const unsigned hi = __shfl_sync(0xFFFFFFFFu, shi, e);
+    const int first = __shfl_sync(0xFFFFFFFFu, pre, e);
+    nbrow = __shfl_sync(0xFFFFFFFFu, nbr, e);
+    wsign = __shfl_sync(0xFFFFFFFFu, wsg, e);
+    const int g = g0 + lane;
+    if (g < total) {
+      const uint4* p = reinterpret_cast<const uint4*>((((unsigned long long)hi << 32) | lo)) +
+                       2 * (g - first);
+      r0 = __ldcs(p);
+      r1 = __ldcs(p + 1);
+    }
+  };
+
+  uint4 c0, c1, n0, n1;
+  uint32_t cnb, nnb;
+  float cws, nws;
+  fetch(0, c0, c1, cnb, cws);
+  for (int g0 = 0; g0 < total; g0 += 32) {
+    fetch(g0 + 32, n0, n1, nnb, nws);
 #pragma unroll
-    for (int u = 0; u < INFL; ++u) {
-      const int un = u0 + INFL + u;
-      nxt[u][0] = nxt[u][1] = make_uint4(0u, 0u, 0u, 0u);
-      if (un < units) {
-        nxt[u][0] = __ldcs(it.src + 2 * un);
-        nxt[u][1] = __ldcs(it.src + 2 * un + 1);
+    for (int h = 0; h < 2; ++h) {
+      const uint4 r = h ? c1 : c0;
+      if (PREC == SNN_EXACT_F16W) {
+        deliver_f16(r.x, cnb, cws, acc, pol);
+        deliver_f16(r.y, cnb, cws, acc, pol);
+        deliver_f16(r.z, cnb, cws, acc, pol);
+        deliver_f16(r.w, cnb, cws, acc, pol);
+      } else {
+        deliver_f32(r.x, (int32_t)r.y, wg, win_s, P, pol);
+        deliver_f32(r.z, (int32_t)r.w, wg, win_s, P, pol);
       }
     }
-#pragma unroll
-    for (int u = 0; u < INFL; ++u) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint4 r = cur[u][h];
-        if (PREC == SNN_EXACT_F16W) {
-          deliver_f16(r.x, nbrow, wsign, P, pol);
-          deliver_f16(r.y, nbrow, wsign, P, pol);
-          deliver_f16(r.z, nbrow, wsign, P, pol);
-          deliver_f16(r.w, nbrow, wsign, P, pol);
-        } else {
-          deliver_f32(r.x, (int32_t)r.y, wg, win_s, P, pol);
-          deliver_f32(r.z, (int32_t)r.w, wg, win_s, P, pol);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < INFL; ++u) {
-      cur[u][0] = nxt[u][0];
-      cur[u][1] = nxt[u][1];
-    }
+    c0 = n0;
+    c1 = n1;
+    cnb = nnb;
+    cws = nws;
   }
 }
 
@@ -877,7 +892,7 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
         if (lane == 0) k1 = atomicAdd(&S.next, (unsigned)kBatchItems);
         k1 = a + __shfl_sync(0xFFFFFFFFu, k1, 0);
         const Item nxt = resolve_item<PREC>(P, k1 + lane, b, S, tab, n_entries, nb_s);
-        stream_items<PREC, INFL>(P, cur, win_s, wg, pol);
+        stream_items<PREC>(P, cur, win_s, wg, pol);
         cur = nxt;
         k0 = k1;
       }
