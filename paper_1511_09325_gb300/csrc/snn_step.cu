@@ -192,7 +192,33 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
                              ? P.ccnt + (s_in % P.nslot) * P.ncol : nullptr;
   const unsigned* cout_ = P.ccnt != nullptr ? P.ccnt + ((t + 1) % P.nslot) * P.ncol : nullptr;
 
+  // the state of the body's next tile is requested before the current tile
+  // is processed, so its latency overlaps the current tile's work
+  float4 pv = make_float4(0.f, 0.f, 0.f, 0.f), pc = pv;
+  uchar4 pr = make_uchar4(0, 0, 0, 0);
+  int4 pa = make_int4(0, 0, 0, 0);
+  {
+    const long long q0 = (long long)vb * kUpdateThreads + tid;
+    if (vb < tiles && q0 * 4 < P.N) {
+      pv = ld_stream(reinterpret_cast<const float4*>(P.V) + q0);
+      pc = ld_stream(reinterpret_cast<const float4*>(P.C) + q0);
+      pr = ld_stream(reinterpret_cast<const uchar4*>(P.R) + q0);
+      pa = ld_stream(reinterpret_cast<const int4*>(P.acc) + q0);
+    }
+  }
   for (long long tile = vb; tile < tiles; tile += vgrid) {
+    const float4 v4 = pv, c4 = pc;
+    const uchar4 r4 = pr;
+    const int4 a4 = pa;
+    {
+      const long long qn = (tile + vgrid) * kUpdateThreads + tid;
+      if (tile + vgrid < tiles && qn * 4 < P.N) {
+        pv = ld_stream(reinterpret_cast<const float4*>(P.V) + qn);
+        pc = ld_stream(reinterpret_cast<const float4*>(P.C) + qn);
+        pr = ld_stream(reinterpret_cast<const uchar4*>(P.R) + qn);
+        pa = ld_stream(reinterpret_cast<const int4*>(P.acc) + qn);
+      }
+    }
     const long long first = tile * kTile;
     const long long last = (first + kTile < P.N ? first + kTile : P.N) - 1;
     // neuron indices are below 2^31: 32-bit divisions are exact (and cheap)
@@ -210,10 +236,6 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
     int scol[4] = {-1, -1, -1, -1};
     if (i0 < P.N) {
       const uint4 x = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)t, kTagExt, 0u), P.seed_lo, P.seed_hi);
-      const float4 v4 = ld_stream(reinterpret_cast<const float4*>(P.V) + q);
-      const float4 c4 = ld_stream(reinterpret_cast<const float4*>(P.C) + q);
-      const uchar4 r4 = ld_stream(reinterpret_cast<const uchar4*>(P.R) + q);
-      const int4 a4 = ld_stream(reinterpret_cast<const int4*>(P.acc) + q);
       reinterpret_cast<int4*>(P.acc)[q] = make_int4(0, 0, 0, 0);
       const float vin[4] = {v4.x, v4.y, v4.z, v4.w};
       const float cin[4] = {c4.x, c4.y, c4.z, c4.w};
@@ -275,7 +297,9 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
         S.tpos[k] = pos;
         pos += S.tpop[k][0] + S.tpop[k][1];
       }
-      S.cbase = pos ? (long long)atomicAdd(P.cnt + slot, pos) : 0ll;
+      // the compact list (no per-column lists) takes the tile's spikes at a
+      // shared cursor; per-column lists need none
+      S.cbase = (pos && P.ccnt == nullptr) ? (long long)atomicAdd(P.cnt + slot, pos) : 0ll;
       S.rbase = S.rc;
       S.rc += pos;
       S.spk += pos;
@@ -338,7 +362,7 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
   }
 }
 
-__global__ void __launch_bounds__(kUpdateThreads, 5) update_kernel(const StepParams P) {
+__global__ void __launch_bounds__(kUpdateThreads, 4) update_kernel(const StepParams P) {
   __shared__ UpdateSmem S;
   update_body(P, P.ctl->t, (int)blockIdx.x, (int)gridDim.x, S, (int)threadIdx.x, 0);
 }
