@@ -42,11 +42,11 @@ namespace snn {
 namespace {
 
 constexpr int kUpdateThreads = 256;
-constexpr int kDeliverThreads = 1024;  // one delivery block per SM
+constexpr int kDeliverThreads = 768;   // one delivery block per SM (24 warps, 2 rounds in flight)
 constexpr int kBatchThreads = 512;     // batch kernel: 2 update sub-blocks or one delivery block
 constexpr int kUpdateSubs = kBatchThreads / kUpdateThreads;
-constexpr int kInflightF32 = 1;  // 32-byte sectors per lane and stage, F32W (2 loads each)
-constexpr int kInflightF16 = 2;  // the same for F16W (two stages in flight)
+constexpr int kDepthF32 = 2;     // rounds of 32-byte sectors in flight per lane, F32W
+constexpr int kDepthF16 = 2;     // the same, F16W
 constexpr int kTile = kUpdateThreads * 4;    // neurons per update tile
 constexpr int kTileCols = kTile / 2 + 2;     // columns a tile can touch (npc >= 2)
 constexpr int kBatchItems = 32;              // items per warp batch (one per lane)
@@ -605,8 +605,8 @@ __device__ __forceinline__ Item resolve_item(const StepParams& P, unsigned item,
 // in round g0 belongs to the item holding g0 plus the items that start
 // between g0 and g0 + L (a ballot and an or-reduction over the items' first
 // sectors); the item's fields come by shuffle.  The next round's sectors are
-// requested before the current ones are delivered.
-template <int PREC>
+// requested DEPTH rounds ahead of the ones being delivered.
+template <int PREC, int DEPTH>
 __device__ __forceinline__ void stream_items(const StepParams& P, const Item& it, uint32_t win_s,
                                              const WinGeo& wg, uint64_t pol) {
   const int lane = threadIdx.x & 31;
@@ -659,29 +659,33 @@ __device__ __forceinline__ void stream_items(const StepParams& P, const Item& it
     }
   };
 
-  uint4 c0, c1, n0, n1;
-  uint32_t cnb, nnb;
-  float cws, nws;
-  fetch(0, c0, c1, cnb, cws);
-  for (int g0 = 0; g0 < total; g0 += 32) {
-    fetch(g0 + 32, n0, n1, nnb, nws);
+  // a ring of DEPTH stages: stage s holds the round g0 + 32 s and, once it
+  // has been delivered, is refilled with the round DEPTH stages later
+  uint4 a[DEPTH], b[DEPTH];
+  uint32_t nbs[DEPTH];
+  float wss[DEPTH];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint4 r = h ? c1 : c0;
-      if (PREC == SNN_EXACT_F16W) {
-        deliver_f16(r.x, cnb, cws, acc, pol);
-        deliver_f16(r.y, cnb, cws, acc, pol);
-        deliver_f16(r.z, cnb, cws, acc, pol);
-        deliver_f16(r.w, cnb, cws, acc, pol);
-      } else {
-        deliver_f32(r.x, (int32_t)r.y, wg, win_s, P, pol);
-        deliver_f32(r.z, (int32_t)r.w, wg, win_s, P, pol);
+  for (int st = 0; st < DEPTH; ++st) fetch(32 * st, a[st], b[st], nbs[st], wss[st]);
+  for (int g0 = 0; g0 < total; g0 += 32 * DEPTH) {
+#pragma unroll
+    for (int st = 0; st < DEPTH; ++st) {
+      if (g0 + 32 * st < total) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint4 r = h ? b[st] : a[st];
+          if (PREC == SNN_EXACT_F16W) {
+            deliver_f16(r.x, nbs[st], wss[st], acc, pol);
+            deliver_f16(r.y, nbs[st], wss[st], acc, pol);
+            deliver_f16(r.z, nbs[st], wss[st], acc, pol);
+            deliver_f16(r.w, nbs[st], wss[st], acc, pol);
+          } else {
+            deliver_f32(r.x, (int32_t)r.y, wg, win_s, P, pol);
+            deliver_f32(r.z, (int32_t)r.w, wg, win_s, P, pol);
+          }
+        }
       }
+      fetch(g0 + 32 * (st + DEPTH), a[st], b[st], nbs[st], wss[st]);
     }
-    c0 = n0;
-    c1 = n1;
-    cnb = nnb;
-    cws = nws;
   }
 }
 
@@ -916,7 +920,7 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
         if (lane == 0) k1 = atomicAdd(&S.next, (unsigned)kBatchItems);
         k1 = a + __shfl_sync(0xFFFFFFFFu, k1, 0);
         const Item nxt = resolve_item<PREC>(P, k1 + lane, b, S, tab, n_entries, nb_s);
-        stream_items<PREC>(P, cur, win_s, wg, pol);
+        stream_items<PREC, INFL>(P, cur, win_s, wg, pol);
         cur = nxt;
         k0 = k1;
       }
@@ -953,7 +957,7 @@ __global__ void __launch_bounds__(kDeliverThreads, 1) deliver_kernel(const StepP
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ DeliverSmem S;
   const long long t = P.ctl->t;
-  deliver_body<PREC, PREC == SNN_EXACT_F16W ? kInflightF16 : kInflightF32, kDeliverThreads>(
+  deliver_body<PREC, PREC == SNN_EXACT_F16W ? kDepthF16 : kDepthF32, kDeliverThreads>(
       P, t, (int)blockIdx.x, (int)gridDim.x, S, s_dyn);
 
   // the last block to finish closes the step
@@ -1257,9 +1261,11 @@ template <int PREC, int INFL>
 void* batch_fn() {
   return reinterpret_cast<void*>(batch_kernel<PREC, INFL>);
 }
+// The batch tuner's schedule `infl` (2 or 4) selects 1 or 2 rounds of
+// sectors in flight per lane.
 void* batch_kernel_ptr(int precision, int infl) {
-  if (precision == SNN_EXACT_F16W) return infl == 2 ? batch_fn<1, 2>() : batch_fn<1, 4>();
-  return infl == 2 ? batch_fn<0, 2>() : batch_fn<0, 4>();
+  if (precision == SNN_EXACT_F16W) return infl == 2 ? batch_fn<1, 1>() : batch_fn<1, 2>();
+  return infl == 2 ? batch_fn<0, 1>() : batch_fn<0, 2>();
 }
 }  // namespace
 
