@@ -472,32 +472,36 @@ __device__ __forceinline__ unsigned long long block_scan(unsigned long long v, D
   return before + incl - v;
 }
 
-// One F16W record w = half_magnitude(15) << 17 | offset(6) << 11 | l(11),
-// as one PTX block: the offset picks, in the neighbour-table row `nbrow` of
-// the spiker's column, the target column -- its shared-window address, or
-// bit 31 set and its first neuron in the accumulator; the weight
+// Neighbour-table entry of F16W record w = half_magnitude(15) << 17 |
+// offset(6) << 11 | l(11): in the row `nbrow` of the spiker's column, the
+// offset's target column -- its shared-window address, or bit 31 set and its
+// first neuron in the accumulator.  The entries of a sector's eight records
+// are loaded before any of them is delivered, so the loads are not ordered
+// behind the shared-memory reductions.
+__device__ __forceinline__ uint32_t nb_entry(uint32_t w, uint32_t nbrow) {
+  uint32_t e;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(e) : "r"(nbrow + ((w >> 9) & 0xFCu)));
+  return e;
+}
+
+// Deliver F16W record w with its table entry e, as one PTX block: the weight
 // rint(half * 2^16) comes from one rounded multiply-add (x * (+-2^16) +
 // 1.5 * 2^23 lands in [2^23, 2^24), where the float grid is the integers, so
 // the low mantissa bits hold the rounded product); one setp gives both
-// predicates, and zero weights (padding records, unused lanes) deliver
-// nothing.  No compiler memory barrier: nothing this loop reads aliases the
-// window or the accumulator.
-__device__ __forceinline__ void deliver_f16(uint32_t w, uint32_t nbrow, float wsign,
+// predicates; zero weights (padding records, unused lanes) deliver nothing.
+// No compiler memory barrier: nothing the loop reads aliases the window or
+// the accumulator.
+__device__ __forceinline__ void deliver_f16(uint32_t w, uint32_t e, float wsign,
                                             const int32_t* acc, uint64_t pol) {
   asm volatile(
       "{\n\t"
-      ".reg .u32 t, e, l4, sa, go;\n\t"
+      ".reg .u32 t, l, sa, go;\n\t"
       ".reg .b16 h, hh;\n\t"
       ".reg .f32 hf, x;\n\t"
       ".reg .s32 wfx;\n\t"
       ".reg .u64 ga;\n\t"
       ".reg .pred pon, pg, ps;\n\t"
-      "shr.b32 t, %0, 9;\n\t"
-      "and.b32 t, t, 252;\n\t"
-      "add.u32 t, t, %1;\n\t"
-      "ld.shared.u32 e, [t];\n\t"
-      "shl.b32 l4, %0, 2;\n\t"
-      "and.b32 l4, l4, 8188;\n\t"
+      "and.b32 l, %0, 2047;\n\t"
       "shr.b32 t, %0, 17;\n\t"
       "mov.b32 {h, hh}, t;\n\t"
       "cvt.f32.f16 hf, h;\n\t"
@@ -505,16 +509,15 @@ __device__ __forceinline__ void deliver_f16(uint32_t w, uint32_t nbrow, float ws
       "mov.b32 wfx, x;\n\t"
       "sub.s32 wfx, wfx, 1262485504;\n\t"
       "setp.ne.s32 pon, wfx, 0;\n\t"
-      "setp.lt.and.s32 pg|ps, e, 0, pon;\n\t"
-      "add.u32 sa, e, l4;\n\t"
+      "setp.lt.and.s32 pg|ps, %1, 0, pon;\n\t"
+      "mad.lo.u32 sa, l, 4, %1;\n\t"
       "@ps red.shared.add.s32 [sa], wfx;\n\t"
-      "shl.b32 go, e, 2;\n\t"
-      "add.u32 go, go, l4;\n\t"
-      "cvt.u64.u32 ga, go;\n\t"
-      "add.u64 ga, ga, %3;\n\t"
+      "add.u32 go, %1, l;\n\t"
+      "and.b32 go, go, 2147483647;\n\t"
+      "mad.wide.u32 ga, go, 4, %3;\n\t"
       "@pg red.global.add.L2::cache_hint.s32 [ga], wfx, %4;\n\t"
       "}" ::"r"(w),
-      "r"(nbrow), "f"(wsign), "l"(acc), "l"(pol));
+      "r"(e), "f"(wsign), "l"(acc), "l"(pol));
 }
 
 // F32W record {target neuron, round(w * 2^16)}: the target's column is tested
@@ -670,15 +673,18 @@ __device__ __forceinline__ void stream_items(const StepParams& P, const Item& it
 #pragma unroll
     for (int st = 0; st < DEPTH; ++st) {
       if (g0 + 32 * st < total) {
+        if (PREC == SNN_EXACT_F16W) {
+          const uint32_t w8[8] = {a[st].x, a[st].y, a[st].z, a[st].w,
+                                  b[st].x, b[st].y, b[st].z, b[st].w};
+          uint32_t e8[8];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint4 r = h ? b[st] : a[st];
-          if (PREC == SNN_EXACT_F16W) {
-            deliver_f16(r.x, nbs[st], wss[st], acc, pol);
-            deliver_f16(r.y, nbs[st], wss[st], acc, pol);
-            deliver_f16(r.z, nbs[st], wss[st], acc, pol);
-            deliver_f16(r.w, nbs[st], wss[st], acc, pol);
-          } else {
+          for (int q = 0; q < 8; ++q) e8[q] = nb_entry(w8[q], nbs[st]);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) deliver_f16(w8[q], e8[q], wss[st], acc, pol);
+        } else {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint4 r = h ? b[st] : a[st];
             deliver_f32(r.x, (int32_t)r.y, wg, win_s, P, pol);
             deliver_f32(r.z, (int32_t)r.w, wg, win_s, P, pol);
           }
