@@ -1,11 +1,14 @@
 """Benchmark: synaptic events/s of the column-network step on GB300.
 
 A bench step is one 1 ms simulation step (neuron update + spike delivery) of
-the 24x24-column network (714 240 neurons, 885.7 M synapses, FP32 weights,
-seed 2) unless --workload names another one.  Prints one JSON line.
+the 96x96-column network (11.43 M neurons, 14.17 G synapses, FP16 weights,
+seed 3) unless --workload names another one.  The network first runs
+--settle untimed steps (past the initial synchronous volley), then W warm-up
+steps, then the K timed steps; the line reports that window's own activity.
+Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                  [--impl ours|reference] [--no-extra]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--settle S]
+                  [--workload NAME] [--impl ours|reference] [--no-extra]
 
 N > 1 runs N independent replicas (one network per GPU, seed + rank), launched
 with torch.distributed.run; rank 0 prints the whole-job line.
@@ -32,9 +35,11 @@ UNIT = "events/s"
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=100)
-    ap.add_argument("--workload", default="cols24x24_f32w")
+    ap.add_argument("--workload", default="cols96x96_f16w")
+    ap.add_argument("--settle", type=int, default=2000,
+                    help="untimed steps after the build, before the warm-up")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 96x96 FP16-vs-FP32 comparison and the batched form")
@@ -61,9 +66,10 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _traffic(workload, kernel):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, or
-    None when there is none or the kernel source changed since it was taken."""
+def _traffic(workload, window, kernel):
+    """DRAM bytes per launch of a kernel over exactly this window (workload,
+    settle, warm-up and timed steps) from the committed ncu summary, or None
+    when there is none or the kernel source changed since it was taken."""
     import hashlib
 
     try:
@@ -74,7 +80,10 @@ def _traffic(workload, kernel):
             digest = hashlib.sha256(f.read()).hexdigest()
         if not digest.startswith(t.get("kernel_sha256", "-")):
             return None
-        return t.get(workload, {}).get(kernel)
+        w = t.get(workload, {})
+        if [w.get("settle"), w.get("warmup"), w.get("steps")] != list(window):
+            return None
+        return w.get(kernel)
     except Exception:
         return None
 
@@ -161,11 +170,19 @@ def any_rank(dist, flag, device):
     return bool(t.item())
 
 
+# The oracle's sample of each workload: the same construction on a grid the
+# oracle steps in seconds (one oracle step of the 96x96 network takes about a
+# minute).
+CPU_SLICE = {"cols96x96_f16w": "cols48x48_f16w", "cols96x96_f32w": "cols48x48_f32w"}
+
+
 def _cpu_baseline(workload, seconds_target=15.0):
-    """The oracle, as it stands, on a bounded sample of the workload."""
+    """The oracle, as it stands, on a bounded sample of the workload: the
+    first steps of its CPU slice from the initial state."""
     import oracle
 
-    cfg = W.WORKLOADS[workload]
+    sample = CPU_SLICE.get(workload, workload)
+    cfg = W.WORKLOADS[sample]
     n, s = W.neuron_params(), W.synapse_params(**cfg.get("synapse", {}))
     p = oracle.make_params(cfg["grid_w"], cfg["grid_h"], n, s, cfg["seed"])
     mode = cfg["precision"]
@@ -181,8 +198,8 @@ def _cpu_baseline(workload, seconds_target=15.0):
     events = float(len(o["t"])) * s["k_out"]
     return {"value": events / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%s, first %d steps from the initial state (%d spikes), single thread"
-                      % (workload, steps, len(o["t"])),
-            "seconds": dt, "all_cores": _cpu_all_cores(workload, steps)}
+                      % (sample, steps, len(o["t"])),
+            "seconds": dt, "all_cores": _cpu_all_cores(sample, steps)}
 
 
 # One oracle process: set up, report ready, wait for the start line, run the
@@ -237,23 +254,59 @@ def _cpu_all_cores(workload, steps):
                       % (cores, steps, workload)}
 
 
+# Reference arm: the oracle on the workload's CPU slice; each bench step is one
+# oracle step, so the driver's K and W set the length of the run.
+REF_SLICE = {"cols96x96_f16w": "cols24x24_f16w", "cols96x96_f32w": "cols24x24_f32w",
+             "cols48x48_f16w": "cols24x24_f16w", "cols48x48_f32w": "cols24x24_f32w"}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    cb = _cpu_baseline(args.workload)
-    cfg = W.WORKLOADS[args.workload]
+    import oracle
+
+    sample = REF_SLICE.get(args.workload, args.workload)
+    cfg = W.WORKLOADS[sample]
+    n, s = W.neuron_params(), W.synapse_params(**cfg.get("synapse", {}))
+    p = oracle.make_params(cfg["grid_w"], cfg["grid_h"], n, s, cfg["seed"])
+    oracle.build()
+    wu = max(args.warmup, 0)
+    t0 = time.perf_counter()
+    if wu:
+        oracle.run(p, cfg["precision"], wu, want_state=False)
+    t1 = time.perf_counter()
+    o2 = oracle.run(p, cfg["precision"], wu + args.steps, want_state=False)
+    t2 = time.perf_counter()
+    # timed: the K steps after the W warm-up ones (the second run repeats the
+    # warm-up, whose time the first run measured)
+    secs = max((t2 - t1) - (t1 - t0), 1e-9)
+    spikes = int(o2["step_spikes"][wu:].sum())
+    value = spikes * s["k_out"] / secs
+    main = W.WORKLOADS[args.workload]
     line = {
-        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": cfg["precision"],
-        "data": "synthetic", "config": {"workload": args.workload},
-        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample",
-                                             "all_cores")},
-        "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
+        "ms_per_step": secs * 1e3 / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+i32" if main["precision"] == "f32w" else "f16+i32",
+        "data": "synthetic", "config": _config(args, main, None, args.gpus),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%s (the workload's construction at %dx%d), steps %d..%d "
+                                   "from the initial state, single thread"
+                                   % (sample, cfg["grid_w"], cfg["grid_h"], wu,
+                                      wu + args.steps - 1)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def _config(args, cfg, info=None, ws=1):
+    """The config object of the JSON line (the same for both arms)."""
+    return {"workload": args.workload, "grid": [cfg["grid_w"], cfg["grid_h"]],
+            "precision": cfg["precision"], "seed": cfg["seed"], "parallelism": "replicas%d" % ws,
+            "settle_steps": getattr(args, "settle", 0),
+            "l2": "inputs larger than L2 (the synapse table)"}
 
 
 def reduce_ranks(dist, ms, rec_ev, ext_ev, device):
@@ -296,27 +349,34 @@ def _timed(net, torch, stream, steps, barrier=None):
     return ms, r1 - r0, e1 - e0
 
 
-def _kernel_roofline(snn, torch, cfg, seed, stream, warmup, P, workload):
+def _kernel_roofline(snn, torch, cfg, seed, stream, lead, P, workload, window):
     """Per-kernel device time and algorithmic bytes over the timed window.
 
     A second net with the same seed replays the identical window (the
-    simulation is deterministic) with every kernel bracketed by CUDA events
-    on the net's stream."""
+    simulation is deterministic: `lead` untimed steps, then the P timed ones)
+    with every kernel bracketed by CUDA events on the net's stream."""
     twin, _ = _build_net(snn, torch, cfg, seed, stream)
-    twin.step(warmup)
+    twin.step(lead)
+    twin.spikes()
     kms, kbytes = twin.step_profiled(P)
     twin.close()
+    torch.cuda.empty_cache()
     hbm, peak_kind = _peaks()
     dom = 0 if kms[0] >= kms[1] else 1
     kname = ["update_kernel", "deliver_kernel"][dom]
     achieved = kbytes[dom] / (kms[dom] * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-            "traffic": _traffic(workload, kname), "launches": P,
+            "traffic": _traffic(workload, window, kname), "launches": P,
             "kernel_ms": {"update": kms[0] / P, "deliver": kms[1] / P},
             "kernel_gbs": {"update": kbytes[0] / (kms[0] * 1e-3) / 1e9,
                            "deliver": kbytes[1] / (kms[1] * 1e-3) / 1e9},
-            "algorithmic_bytes_per_launch": {"update": kbytes[0] / P, "deliver": kbytes[1] / P}}
+            "kernel_frac": {"update": kbytes[0] / (kms[0] * 1e-3) / 1e9 / hbm,
+                            "deliver": kbytes[1] / (kms[1] * 1e-3) / 1e9 / hbm},
+            "algorithmic_bytes_per_launch": {"update": kbytes[0] / P, "deliver": kbytes[1] / P},
+            "bytes_model": "update 26 B per neuron + 12 B per spike; deliver per spike k_out x "
+                           "record bytes (4 B FP16 record: 15-bit weight + 17-bit target; 8 B "
+                           "FP32 record) + 6 B per delay bucket (descriptor id and bucket end)"}
 
 
 def _e2e(net, torch, E, dist=None, device="cuda"):
@@ -373,35 +433,47 @@ def run_ours(args):
     cfg = W.WORKLOADS[args.workload]
     stream = torch.cuda.Stream()
     seed = cfg["seed"] + rank
-    K, Wm = args.steps, args.warmup
+    K, Wm, S = args.steps, args.warmup, args.settle
 
     clocks = Clocks(uuid)
     clocks.start()
     net, build_s = _build_net(snn, torch, cfg, seed, stream)
+    net.step(S)
+    net.spikes()
     net.step(Wm)
     net.spikes()
+    net.rates()  # opens the rate window of the timed steps
     ms, rec_ev, ext_ev = _timed(net, torch, stream, K, dist.barrier if dist else None)
     clk = clocks.stop()
+    remeasured = False
     if any_rank(dist, clocks_rejected(clk), "cuda"):
         # a slowed or locked clock disqualifies the window: time the next one
+        remeasured = True
+        net.rates()
         clocks = Clocks(uuid)
         clocks.start()
         ms, rec_ev, ext_ev = _timed(net, torch, stream, K, dist.barrier if dist else None)
         clk = clocks.stop()
-        if clk is not None:
-            clk["remeasured"] = True
+    if clk is not None:
+        clk["remeasured"] = remeasured
+        clk["rejected"] = bool(clocks_rejected(clk))
+    _, pop_hz = net.rates()
+    spikes_window = rec_ev / W.SYNAPSE["k_out"]
     if dist:
         ms, rec_ev, ext_ev = reduce_ranks(dist, ms, rec_ev, ext_ev, "cuda")
     info = net.info()
-    _, pop_hz = net.rates()
     e2e = _e2e(net, torch, max(1, min(args.e2e_steps, max(K, 1))), dist)
     net.close()
+    torch.cuda.empty_cache()
     P = K if args.profile_steps is None else min(args.profile_steps, K)
-    roofline = _kernel_roofline(snn, torch, cfg, seed, stream, Wm, max(1, P), args.workload)
+    lead = S + Wm + (K if remeasured else 0)
+    roofline = _kernel_roofline(snn, torch, cfg, seed, stream, lead, max(1, P), args.workload,
+                                (S, Wm, K))
 
-    extra = batched = surrogate = paper = None
+    extra = batched = surrogate = paper = crit = None
     if not args.no_extra and ws == 1:
-        extra = _precision_form(snn, torch, stream, Wm)
+        extra = _precision_form(snn, torch, stream, S)
+        crit = _fp64_criterion(snn, torch, stream)
         batched = _batched_form(snn, torch, stream)
         surrogate = _surrogate_form(snn, torch, stream)
         paper = _paper_form(snn, torch, stream, Wm)
@@ -419,15 +491,16 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+i32" if cfg["precision"] == "f32w" else "f16+i32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "grid": [cfg["grid_w"], cfg["grid_h"]],
-                       "neurons": info["neurons"], "synapses": info["synapses"],
-                       "precision": cfg["precision"], "seed": cfg["seed"],
-                       "parallelism": "replicas%d" % ws,
-                       "l2": "inputs larger than L2 (synapse table %.1f GB)"
-                             % (info["synapse_bytes"] / 1e9)},
+            "config": _config(args, cfg, None, args.gpus),
+            "window": {"first_step": lead, "steps": K,
+                       "state": "after %d settle and %d warm-up steps (model time %.3f s)"
+                                % (S, Wm, lead * 1e-3),
+                       "spikes_per_step": spikes_window / K,
+                       "pop_hz": [float(pop_hz[0]), float(pop_hz[1])]},
+            "neurons": info["neurons"], "synapses": info["synapses"],
+            "synapse_table_gb": info["synapse_bytes"] / 1e9,
             "wall_s_per_model_s": ms / K,
             "paper_convention_events_per_s": (rec_ev + ext_ev) / (ms * 1e-3),
-            "pop_rates_hz": [float(pop_hz[0]), float(pop_hz[1])],
             "build_s": build_s,
             "gpu_launches": 2 * K,
             "roofline": roofline,
@@ -437,6 +510,8 @@ def run_ours(args):
         }
         if extra:
             line["precision_form"] = extra
+        if crit:
+            line["fp64_criterion"] = crit
         if batched:
             line["batched_form"] = batched
         if surrogate:
@@ -488,7 +563,7 @@ def _batched_form(snn, torch, stream, steps=2000, n_nets=64):
     out["build_s"] = time.perf_counter() - t0
     choice = b.tune(25)
     out["tuned_choice"] = choice
-    out["tuned_schedule"] = {"chunks_in_flight": [4, 4, 2, 2][choice % 4],
+    out["tuned_schedule"] = {"sector_rounds_in_flight": [2, 2, 1, 1][choice % 4],
                              "windows": choice % 2 == 0,
                              "delivery_blocks_per_column": [8, 4, 2, 1][choice // 4]}
     tuned_steps = 2 * 2 * 4 * 25  # two stages of two rounds of four candidates
@@ -545,34 +620,106 @@ def _batch_bytes(grids, neurons, synapses, events, steps):
     return total
 
 
-def _precision_form(snn, torch, stream, warmup, steps=1000):
-    """96x96 columns (14.17 G synapses), FP16 weights vs FP32 weights."""
-    out = {"workload": "cols96x96", "steps": steps, "warmup": warmup}
+def _precision_form(snn, torch, stream, settle, steps=2000):
+    """96x96 columns (14.17 G synapses), FP16 weights vs FP32 weights: the
+    same network (seed 3) after `settle` untimed steps, then `steps` timed
+    graph-replayed steps (about two Up/Down cycles), then the first 500 of the
+    following steps with per-kernel events."""
+    out = {"workload": "cols96x96", "settle": settle, "steps": steps}
     free, _ = torch.cuda.mem_get_info()
     for prec in ("f16w", "f32w"):
         cfg = W.WORKLOADS["cols96x96_" + prec]
-        need = 11427840 * (1384 * (4 if prec == "f16w" else 8) + 140)
+        need = 11427840 * (1384 * (4 if prec == "f16w" else 8) + 140 + 21 * 32)
         if need > free * 0.97:
             out[prec] = {"skipped": "needs %.0f GB of %.0f GB free" % (need / 1e9, free / 1e9)}
             continue
         net, build_s = _build_net(snn, torch, cfg, cfg["seed"], stream)
-        net.step(warmup)
+        net.step(settle)
         net.spikes()
+        net.rates()
         ms, rec_ev, ext_ev = _timed(net, torch, stream, steps)
         _, pop = net.rates()
+        net.spikes()
         kms, kb = net.step_profiled(min(steps, 500))
         hbm, _ = _peaks()
         gbs = (kb[0] + kb[1]) / ((kms[0] + kms[1]) * 1e-3) / 1e9
         out[prec] = {"events_per_s": rec_ev / (ms * 1e-3), "wall_s_per_model_s": ms / steps,
                      "ms_per_step": ms / steps, "build_s": build_s,
+                     "spikes_per_step": rec_ev / W.SYNAPSE["k_out"] / steps,
                      "pop_rates_hz": [float(pop[0]), float(pop[1])],
                      "step_gbs": gbs, "step_frac_hbm": gbs / hbm,
                      "deliver_gbs": kb[1] / (kms[1] * 1e-3) / 1e9,
+                     "deliver_frac_hbm": kb[1] / (kms[1] * 1e-3) / 1e9 / hbm,
                      "update_gbs": kb[0] / (kms[0] * 1e-3) / 1e9}
         net.close()
         torch.cuda.empty_cache()
     if "events_per_s" in out.get("f16w", {}) and "events_per_s" in out.get("f32w", {}):
         out["fp16_speedup_wall"] = out["f32w"]["ms_per_step"] / out["f16w"]["ms_per_step"]
+    return out
+
+
+def _fp64_criterion(snn, torch, stream, n_seeds=256):
+    """The rate / ISI-CV criterion against the FP64 model on the first
+    n_seeds networks of the stored FP64 ensemble (2x2 columns, 10 s after a
+    0.5 s transient; tests/golden/fp64_ensemble_2x2.json, written by the
+    oracle): each path runs the same networks through the batched form, and
+    the ensemble-mean relative errors come with their paired standard
+    errors."""
+    import numpy as np
+
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import fp64_ensemble as F
+
+    path = os.path.join(ROOT, "tests", "golden", "fp64_ensemble_2x2.json")
+    with open(path) as f:
+        gold = json.load(f)
+    rows_ref = gold["rows"][:n_seeds]
+    seeds = [r["seed"] for r in rows_ref]
+    n, s = W.neuron_params(), W.synapse_params()
+    ncols = F.GRID[0] * F.GRID[1]
+    secs = F.STEPS / 1000.0
+
+    def obs(rows):
+        return {"rate_e": np.array([r["spikes_e"] for r in rows]) / (n["n_exc"] * ncols * secs),
+                "rate_i": np.array([r["spikes_i"] for r in rows])
+                          / ((n["n_per_col"] - n["n_exc"]) * ncols * secs),
+                "cv_e": np.array([r["cv_e"] for r in rows]),
+                "cv_i": np.array([r["cv_i"] for r in rows])}
+
+    ref = obs(rows_ref)
+    out = {"networks": len(seeds), "model_s": secs, "transient_s": F.TRANSIENT / 1000.0,
+           "reference": "FP64 oracle, %s" % os.path.relpath(path, ROOT),
+           "bounds": {"rates": 0.02, "isi_cv": 0.05}}
+    for prec in ("f16w", "f32w"):
+        rows = []
+        t0 = time.perf_counter()
+        with snn.Batch([F.GRID] * len(seeds), [n] * len(seeds), [s] * len(seeds), seeds, prec,
+                       stream=stream.cuda_stream) as b:
+            for m in b.members:
+                m.set_record_capacity(1 << 20)
+            ts = [[] for _ in seeds]
+            ids = [[] for _ in seeds]
+            done, total = 0, F.TRANSIENT + F.STEPS
+            while done < total:
+                k = min(1000, total - done)
+                b.step(k)
+                done += k
+                for j, m in enumerate(b.members):
+                    t, i, _ = m.spikes()
+                    ts[j].append(t)
+                    ids[j].append(i)
+        for j in range(len(seeds)):
+            rows.append(F.stats(np.concatenate(ts[j]), np.concatenate(ids[j]), n["n_per_col"],
+                                n["n_exc"], ncols, F.TRANSIENT, F.TRANSIENT + F.STEPS))
+        got = obs(rows)
+        res = {"seconds": time.perf_counter() - t0}
+        for k in ref:
+            g, f = got[k], ref[k]
+            ok = np.isfinite(g) & np.isfinite(f)
+            res[k] = {"rel_error": float(g[ok].mean() / f[ok].mean() - 1.0),
+                      "paired_se": float(np.std(g[ok] - f[ok], ddof=1) / np.sqrt(ok.sum())
+                                         / f[ok].mean())}
+        out[prec] = res
     return out
 
 
