@@ -209,6 +209,77 @@ int snn_debug_offset_count(snn_net* net, int64_t column, int32_t delta, int32_t 
 int snn_info(snn_net* net, int64_t* info, int n);
 
 /*
+ * Column-tile shards.  The paper distributes the grid's columns over MPI
+ * processes that exchange the step's spikes every step (Sec. 2, Sec. 3).  A
+ * shard is the part of the network one process (one GPU) holds: the columns
+ * of its tile [x0, x0 + w) x [y0, y0 + h) of the grid_w x grid_h grid, and
+ * the rows of the neurons within stencil_radius columns of it (the halo,
+ * periodic), restricted to the synapses that end in the tile.  Every random
+ * draw uses global neuron indices, so the shards of a partition of the grid,
+ * stepped together, compute exactly the raster and states of the whole
+ * network built by snn_build with the same parameters and seed.
+ *
+ * A step of a shard has two halves.  snn_shard_update runs the neuron update
+ * of the tile's columns for step t; snn_read_spikes then returns the tile's
+ * spikes of step t (global indices).  The caller exchanges them among the
+ * shards (any transport: every shard may receive every shard's spikes) and
+ * passes the received indices to snn_shard_deliver, which lists those of the
+ * halo's columns and delivers all spikes due at step t into the tile's input
+ * of step t + 1.  Because d_min >= 1, one exchange per step suffices.
+ */
+
+/*
+ * snn_build_shard -- build the shard of tile (x0, y0, w, h) of a grid_w x
+ * grid_h network; the other arguments as for snn_build.  The local grid is
+ * the tile plus a halo of stencil_radius columns on each side, or the whole
+ * grid side where tile and halo would cover it.  Requires SNN_CONN_FIXED and
+ * n_per_col a multiple of 4 (SNN_EINVAL otherwise, and for a tile outside the
+ * grid).  On a shard, snn_get_state, snn_read_rates, snn_read_synapses,
+ * snn_row_lengths and snn_debug_offset_count index the local grid (columns
+ * c = ly * local_w + lx, neurons c * n_per_col + l; snn_shard_info gives the
+ * mapping; a row holds only the synapses that end in the tile, F32W targets
+ * as local indices); snn_read_spikes returns global indices; snn_read_rates'
+ * population rates average over the tile's columns; snn_stats counts k_out
+ * synaptic events per tile spike.  snn_step, snn_step_profiled and
+ * snn_grad_build refuse a shard.
+ */
+int snn_build_shard(int grid_w, int grid_h, int x0, int y0, int w, int h,
+                    const snn_neuron_params* neuron, const snn_synapse_params* synapse,
+                    uint64_t seed, int precision, void* cuda_stream, snn_net** out);
+
+/*
+ * snn_shard_update -- first half of the shard's next step t: the neuron
+ * update of the tile's columns (asynchronous on the net's stream).
+ * SNN_ESTATE if the previous step's snn_shard_deliver has not been called,
+ * for a net that is not a shard, or when the status word is set.
+ */
+int snn_shard_update(snn_net* net);
+
+/*
+ * snn_shard_deliver -- second half of step t: ids[0 .. n) are global indices
+ * of neurons that fired at step t, each at most once (the spikes of the other
+ * shards; indices of the own tile and of columns beyond the halo are
+ * ignored).  ids is host memory when ids_on_device is 0 (the library copies
+ * it before returning: the buffer may be reused at once), else device memory
+ * that must stay unchanged until the net's stream has passed the call.
+ * Lists the halo's spikes and
+ * runs the step's delivery; the step counter then advances.  An index beyond
+ * the network or more than n_per_col indices of one column set the status
+ * word (SNN_ESTATE from the next call that checks it).  SNN_ESTATE when
+ * snn_shard_update is due first.
+ */
+int snn_shard_deliver(snn_net* net, const int32_t* ids, int64_t n, int32_t ids_on_device);
+
+/*
+ * snn_shard_info -- geometry of a shard: geo[0..9] = grid_w, grid_h, local_w,
+ * local_h, ex0, ey0, tx0, ty0, w, h: local column (lx, ly) is global column
+ * ((ex0 + lx) mod grid_w, (ey0 + ly) mod grid_h); the tile is local columns
+ * [tx0, tx0 + w) x [ty0, ty0 + h).  n = entries available (at most 10).
+ * SNN_ESTATE for a net that is not a shard.
+ */
+int snn_shard_info(snn_net* net, int32_t* geo, int n);
+
+/*
  * snn_step_profiled -- like snn_step, but each step's kernels are launched
  * one by one with CUDA events around each on the net's stream.  Writes the
  * summed device milliseconds of the neuron-update and delivery kernels and,

@@ -74,6 +74,15 @@ struct snn_net {
   int graph_many_steps = 64;
   long long rate_window_start = 0;
   bool in_batch = false;  // stepped only through its snn_batch
+  // shard (snn_build_shard): geometry, the half step due next (0 update,
+  // 1 delivery), and the received spike indices (pinned host stage, device
+  // copy, and an event recorded once the ingest kernel has read them)
+  ShardGeo sg{};
+  int shard_phase = 0;
+  uint32_t* ingest = nullptr;
+  uint32_t* hingest = nullptr;
+  long long ingest_cap = 0;
+  cudaEvent_t ingest_ev = nullptr;
   std::string err;
 };
 
@@ -153,6 +162,9 @@ void release(snn_net* net) {
   if (net->hmap) cudaFreeHost(net->hmap);
   if (net->hstage) cudaFreeHost(net->hstage);
   if (net->hstatus) cudaFreeHost(net->hstatus);
+  if (net->ingest) cudaFree(net->ingest);
+  if (net->hingest) cudaFreeHost(net->hingest);
+  if (net->ingest_ev) cudaEventDestroy(net->ingest_ev);
   void* ptrs[] = {net->syn, net->bend, net->V, net->C, net->R, net->acc,
                   net->desc, net->vcol, net->colv, net->cnt, net->ccnt, net->deg, net->syn_part, net->isum, net->gsum, net->ctl, net->rec, net->rcnt, net->stage, net->dhdr, net->colcnt,
                   net->ext_part, net->spk_part};
@@ -258,7 +270,12 @@ void column_order(int W, int H, int T, std::vector<uint32_t>* vcol, std::vector<
 
 // A kernel found inconsistent counts: the net's stepping is no longer exact.
 int check_status(snn_net* net) {
-  if (net->hstatus && *reinterpret_cast<volatile unsigned*>(net->hstatus) != 0u)
+  const unsigned st = net->hstatus ? *reinterpret_cast<volatile unsigned*>(net->hstatus) : 0u;
+  if (st & kStatusIngest)
+    return fail(net, SNN_ESTATE,
+                "a shard received a spike index beyond the network or more spikes of one column "
+                "than it has neurons; the net's state is no longer exact");
+  if (st != 0u)
     return fail(net, SNN_ESTATE,
                 "a delivery found item counts that disagree with the spike lists; the net's "
                 "state is no longer exact");
@@ -330,8 +347,11 @@ void fill_step_params(snn_net* net) {
   p.hstatus = net->hstatus_dev;
   p.cnt = net->cnt;
   p.ccnt = net->ccnt;
-  p.deg = net->deg;
+  // a shard keeps the out-degree of its rows (synapses into its own columns)
+  // for snn_row_lengths; its spikes count the full k_out synaptic events
+  p.deg = net->sg.on ? nullptr : net->deg;
   p.syn_part = net->syn_part;
+  p.sg = net->sg;
   p.isum = net->isum;
   p.gsum = net->gsum;
   p.bend = net->bend;
@@ -407,8 +427,10 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   bp.plocal_thr = net->tables.plocal_thr;
   std::memcpy(bp.poff_dx, net->tables.poff_dx, sizeof(bp.poff_dx));
   std::memcpy(bp.poff_dy, net->tables.poff_dy, sizeof(bp.poff_dy));
+  bp.sg = net->sg;
   if ((rc = dalloc(net, &net->bend, (size_t)net->N * kBendStride))) return rc;
   net->total_syn = net->N * (long long)net->K;
+  if (net->sg.on && (rc = dalloc(net, &net->deg, (size_t)net->N * 4))) return rc;
   if (net->connectivity == SNN_CONN_PAPER) {
     // count pass: bucket ends, out-degrees and the longest row, which sets
     // the row stride of the table
@@ -506,6 +528,15 @@ int build_impl(snn_net* net, int gw, int gh, const snn_neuron_params* np,
   if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
   cudaFree(wtab);
   if (e != cudaSuccess) return cuda_fail(net, e, "network construction");
+  if (net->sg.on) {
+    // synapses kept by the shard: those into its own columns
+    std::vector<uint32_t> deg((size_t)net->N);
+    SNN_CUDA(net, cudaMemcpyAsync(deg.data(), net->deg, deg.size() * 4, cudaMemcpyDeviceToHost,
+                                  net->stream));
+    SNN_CUDA(net, cudaStreamSynchronize(net->stream));
+    net->total_syn = 0;
+    for (uint32_t d : deg) net->total_syn += d;
+  }
   return SNN_OK;
 }
 
@@ -527,6 +558,7 @@ namespace snn {
 
 int net_view(snn_net* net, NetView* v) {
   if (!net) return SNN_EINVAL;
+  if (net->sg.on) return SNN_ESTATE;
   v->syn = net->syn;
   v->bend = net->bend;
   v->N = net->N;
@@ -554,7 +586,7 @@ namespace {
 int build_net(int grid_w, int grid_h, const snn_neuron_params* neuron,
               const snn_synapse_params* synapse, uint64_t seed, int precision,
               void* cuda_stream, size_t window_budget, unsigned min_items, int part_cols,
-              snn_net** out) {
+              snn_net** out, const ShardGeo* shard = nullptr) {
   if (!out) return fail(nullptr, SNN_EINVAL, "out is NULL");
   *out = nullptr;
   std::string why;
@@ -565,6 +597,7 @@ int build_net(int grid_w, int grid_h, const snn_neuron_params* neuron,
   net->window_budget = window_budget;
   net->min_items = min_items;
   net->part_cols = part_cols;
+  if (shard) net->sg = *shard;
   if (cuda_stream) {
     net->stream = static_cast<cudaStream_t>(cuda_stream);
   } else {
@@ -597,9 +630,110 @@ int snn_build(int grid_w, int grid_h, const snn_neuron_params* neuron,
                    kMinItems, kPartCols, out);
 }
 
+int snn_build_shard(int grid_w, int grid_h, int x0, int y0, int w, int h,
+                    const snn_neuron_params* neuron, const snn_synapse_params* synapse,
+                    uint64_t seed, int precision, void* cuda_stream, snn_net** out) {
+  if (!out) return fail(nullptr, SNN_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  const int vrc = validate(grid_w, grid_h, neuron, synapse, precision, &why);
+  if (vrc != SNN_OK) return fail(nullptr, vrc, why);
+  if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || x0 + w > grid_w || y0 + h > grid_h)
+    return fail(nullptr, SNN_EINVAL, "the shard's tile must lie inside the grid");
+  if (synapse->connectivity != SNN_CONN_FIXED)
+    return fail(nullptr, SNN_EINVAL, "shards support SNN_CONN_FIXED only");
+  if (neuron->n_per_col % 4 != 0)
+    return fail(nullptr, SNN_EINVAL, "shards need n_per_col to be a multiple of 4");
+  // local grid: the tile and a halo as wide as the stencil, or the whole side
+  // where the two would meet
+  const int R = synapse->stencil_radius;
+  ShardGeo g{};
+  g.on = 1;
+  g.GW = grid_w;
+  g.GH = grid_h;
+  g.tw = w;
+  g.th = h;
+  int ew = grid_w, eh = grid_h;
+  if (w + 2 * R < grid_w) {
+    ew = w + 2 * R;
+    g.ex0 = (x0 - R + grid_w) % grid_w;
+    g.tx0 = R;
+  } else {
+    g.ex0 = 0;
+    g.tx0 = x0;
+  }
+  if (h + 2 * R < grid_h) {
+    eh = h + 2 * R;
+    g.ey0 = (y0 - R + grid_h) % grid_h;
+    g.ty0 = R;
+  } else {
+    g.ey0 = 0;
+    g.ty0 = y0;
+  }
+  return build_net(ew, eh, neuron, synapse, seed, precision, cuda_stream, kWindowBudget, kMinItems,
+                   kPartCols, out, &g);
+}
+
+int snn_shard_update(snn_net* net) {
+  if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
+  if (!net->sg.on) return fail(net, SNN_ESTATE, "not a shard: use snn_step");
+  if (net->shard_phase != 0) return fail(net, SNN_ESTATE, "snn_shard_deliver is due first");
+  int rc = check_status(net);
+  if (rc) return rc;
+  SNN_CUDA(net, launch_update(net->sp, net->update_grid, net->stream));
+  net->shard_phase = 1;
+  return SNN_OK;
+}
+
+int snn_shard_deliver(snn_net* net, const int32_t* ids, int64_t n, int32_t ids_on_device) {
+  if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
+  if (!net->sg.on) return fail(net, SNN_ESTATE, "not a shard: use snn_step");
+  if (n < 0 || (n > 0 && !ids)) return fail(net, SNN_EINVAL, "bad spike index array");
+  if (net->shard_phase != 1) return fail(net, SNN_ESTATE, "snn_shard_update is due first");
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(ids);
+  const bool staged = n > 0 && !ids_on_device;
+  if (staged) {
+    // the previous staged indices must have been read before the stage is reused
+    if (net->ingest_ev) SNN_CUDA(net, cudaEventSynchronize(net->ingest_ev));
+    else SNN_CUDA(net, cudaEventCreateWithFlags(&net->ingest_ev, cudaEventDisableTiming));
+    if (n > net->ingest_cap) {
+      const long long want = std::max<long long>(n, 1 << 16);
+      if (net->ingest) cudaFree(net->ingest);
+      if (net->hingest) cudaFreeHost(net->hingest);
+      net->device_bytes -= (size_t)net->ingest_cap * 4;
+      net->ingest = nullptr;
+      net->hingest = nullptr;
+      net->ingest_cap = 0;
+      if (int rc = dalloc(net, &net->ingest, (size_t)want * 4)) return rc;
+      SNN_CUDA(net, cudaMallocHost(&net->hingest, (size_t)want * 4));
+      net->ingest_cap = want;
+    }
+    std::memcpy(net->hingest, ids, (size_t)n * 4);
+    SNN_CUDA(net, cudaMemcpyAsync(net->ingest, net->hingest, (size_t)n * 4, cudaMemcpyHostToDevice,
+                                  net->stream));
+    src = net->ingest;
+  }
+  SNN_CUDA(net, launch_ingest(net->sp, src, n, net->stream));
+  if (staged) SNN_CUDA(net, cudaEventRecord(net->ingest_ev, net->stream));
+  SNN_CUDA(net, launch_deliver(net->sp, net->precision, net->deliver_grid, net->stream));
+  net->shard_phase = 0;
+  return SNN_OK;
+}
+
+int snn_shard_info(snn_net* net, int32_t* geo, int n) {
+  if (!net || !geo) return fail(net, SNN_EINVAL, "null argument");
+  if (!net->sg.on) return fail(net, SNN_ESTATE, "not a shard");
+  const int32_t v[10] = {net->sg.GW, net->sg.GH, net->W, net->H, net->sg.ex0, net->sg.ey0,
+                         net->sg.tx0, net->sg.ty0, net->sg.tw, net->sg.th};
+  for (int i = 0; i < n && i < 10; ++i) geo[i] = v[i];
+  return SNN_OK;
+}
+
 int snn_step(snn_net* net, int64_t n_steps) {
   if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
   if (net->in_batch) return fail(net, SNN_ESTATE, "net belongs to a batch: use snn_batch_step");
+  if (net->sg.on)
+    return fail(net, SNN_ESTATE, "a shard steps by snn_shard_update and snn_shard_deliver");
   if (n_steps < 0) return fail(net, SNN_EINVAL, "n_steps must be >= 0");
   int rc = check_status(net);
   if (rc) return rc;
@@ -620,6 +754,8 @@ int snn_step(snn_net* net, int64_t n_steps) {
 int snn_step_profiled(snn_net* net, int64_t n_steps, double* ms, double* bytes) {
   if (!net) return fail(nullptr, SNN_EINVAL, "net is NULL");
   if (net->in_batch) return fail(net, SNN_ESTATE, "net belongs to a batch: use snn_batch_step");
+  if (net->sg.on)
+    return fail(net, SNN_ESTATE, "a shard steps by snn_shard_update and snn_shard_deliver");
   if (n_steps < 0) return fail(net, SNN_EINVAL, "n_steps must be >= 0");
   std::vector<cudaEvent_t> ev((size_t)n_steps * 3 + 1);
   unsigned long long* dspk = nullptr;  // spikes so far, after each step
@@ -823,6 +959,8 @@ int snn_read_rates(snn_net* net, float* hz, int64_t n, float* pop_hz) {
   net->rate_window_start = c.t;
   const double secs = (double)window * 1e-3;
   const double nE = (double)net->nexc, nI = (double)(net->npc - net->nexc);
+  // a shard's own columns (the halo's spikes are counted by their owners)
+  const double own_cols = net->sg.on ? (double)net->sg.tw * net->sg.th : (double)net->ncol;
   double totE = 0.0, totI = 0.0;
   for (long long k = 0; k < net->ncol; ++k) {
     totE += (double)cnt[2 * k];
@@ -833,8 +971,8 @@ int snn_read_rates(snn_net* net, float* hz, int64_t n, float* pop_hz) {
     }
   }
   if (pop_hz) {
-    pop_hz[0] = (secs > 0 && nE > 0) ? (float)(totE / (nE * net->ncol * secs)) : 0.f;
-    pop_hz[1] = (secs > 0 && nI > 0) ? (float)(totI / (nI * net->ncol * secs)) : 0.f;
+    pop_hz[0] = (secs > 0 && nE > 0) ? (float)(totE / (nE * own_cols * secs)) : 0.f;
+    pop_hz[1] = (secs > 0 && nI > 0) ? (float)(totI / (nI * own_cols * secs)) : 0.f;
   }
   return SNN_OK;
 }

@@ -13,6 +13,11 @@
 // One warp owns one row: a first pass counts the synapses of every delay
 // bucket, a second pass regenerates them and stores each into its bucket in
 // k order (warp match + popc rank), then the bucket tails are padded.
+// A shard (see ShardGeo) draws every synapse with the neuron's global index
+// and keeps only those whose target column is one of its own; an F32W record
+// then holds the target's local index (local and global stencil arithmetic
+// agree for such targets: the halo is as wide as the stencil, or the local
+// grid spans the whole global side).
 #include "snn_device.cuh"
 #include "snn_internal.h"
 
@@ -42,13 +47,36 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
   const uint32_t ndel = (uint32_t)P.ndel;
 
   for (long long j = (long long)blockIdx.x * kBuildWarps + w; j < P.N; j += nwarps) {
-    const uint32_t jj = (uint32_t)j;
+    const int col = (int)((uint32_t)j / (uint32_t)P.npc);
+    const int lj = (int)(j - (long long)col * P.npc);
+    const int cy = col / P.W, cx = col - cy * P.W;
+    int gx, gy;
+    shard_global_col(P.sg, cx, cy, &gx, &gy);
+    const uint32_t jj = P.sg.on ? ((uint32_t)gy * (uint32_t)P.sg.GW + (uint32_t)gx) * (uint32_t)P.npc + (uint32_t)lj
+                                : (uint32_t)j;
+    const bool src_own = shard_owns_global(P.sg, P.W, P.H, gx, gy);
+    // whether synapse k (Philox block x) ends in one of the shard's columns
+    auto kept = [&](int k, const uint4& x) -> bool {
+      if (!P.sg.on) return true;
+      if (k < P.k_local) return src_own;
+      int m = 0;
+      for (int i = 0; i + 1 < P.n_off; ++i) m += (x.y >= s_thr[i]) ? 1 : 0;
+      return shard_owns_global(P.sg, P.W, P.H, wrap(gx + s_dx[m], P.sg.GW), wrap(gy + s_dy[m], P.sg.GH));
+    };
     s_cnt[w][lane] = 0u;
     __syncwarp();
     // pass 1: synapses per delay bucket
+    unsigned nkept = 0u;
     for (int k = lane; k < P.K; k += 32) {
       const uint4 x = philox4x32_10(make_uint4(jj, (uint32_t)k, kTagConn, 0u), P.seed_lo, P.seed_hi);
-      atomicAdd(&s_cnt[w][below(x.z, ndel)], 1u);
+      if (kept(k, x)) {
+        atomicAdd(&s_cnt[w][below(x.z, ndel)], 1u);
+        ++nkept;
+      }
+    }
+    if (P.deg != nullptr) {
+      nkept = __reduce_add_sync(0xFFFFFFFFu, nkept);
+      if (lane == 0) P.deg[j] = nkept;
     }
     __syncwarp();
     const unsigned units = lane < P.ndel ? (s_cnt[w][lane] + (kSlotUnit - 1)) / kSlotUnit : 0u;
@@ -63,14 +91,12 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
     __syncwarp();
 
     const long long row = j * (long long)P.rowcap;
-    const int col = (int)((uint32_t)j / (uint32_t)P.npc);
-    const int lj = (int)(j - (long long)col * P.npc);
     const uint32_t* wt = P.wtab + (lj < P.nexc ? 0 : 65536);
     // pass 2: regenerate and place every synapse
     for (int k0 = 0; k0 < P.K; k0 += 32) {
       const int k = k0 + lane;
-      const bool valid = k < P.K;
       const uint4 x = philox4x32_10(make_uint4(jj, (uint32_t)k, kTagConn, 0u), P.seed_lo, P.seed_hi);
+      const bool valid = k < P.K && kept(k, x);
       const int b = valid ? (int)below(x.z, ndel) : 63;
       uint32_t code;  // F16W: stencil code; F32W: target neuron index
       if (k < P.k_local) {
@@ -85,7 +111,6 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
         if (PREC == SNN_EXACT_F16W) {
           code = ((uint32_t)s_code[m] << 11) | l;
         } else {
-          const int cy = col / P.W, cx = col - cy * P.W;
           const int ty = wrap(cy + s_dy[m], P.H);
           const int tx = wrap(cx + s_dx[m], P.W);
           code = ((uint32_t)ty * (uint32_t)P.W + (uint32_t)tx) * (uint32_t)P.npc + l;
@@ -124,11 +149,22 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
 
 // Initial state: V_i uniform in [0, theta) at 24-bit resolution from word
 // i mod 4 of Philox(i / 4, 0, INIT); calcium, refractoriness and input zero.
+// A shard draws with the global index i (n_per_col is a multiple of 4 there,
+// so a quad of local neurons is a quad of global ones).
 __global__ void __launch_bounds__(256) init_state_kernel(const StepParams P) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long i0 = q * 4;
   if (i0 >= P.N) return;
-  const uint4 u = philox4x32_10(make_uint4((uint32_t)q, 0u, kTagInit, 0u), P.seed_lo, P.seed_hi);
+  uint32_t gq = (uint32_t)q;
+  if (P.sg.on) {
+    const int col = (int)((uint32_t)i0 / (uint32_t)P.npc);
+    const int l = (int)((uint32_t)i0 - (uint32_t)col * (uint32_t)P.npc);
+    const int cy = col / P.W;
+    int gx, gy;
+    shard_global_col(P.sg, col - cy * P.W, cy, &gx, &gy);
+    gq = (((uint32_t)gy * (uint32_t)P.sg.GW + (uint32_t)gx) * (uint32_t)P.npc + (uint32_t)l) >> 2;
+  }
+  const uint4 u = philox4x32_10(make_uint4(gq, 0u, kTagInit, 0u), P.seed_lo, P.seed_hi);
   const float s = 5.9604644775390625e-08f;  // 2^-24
   float4 v;
   v.x = __fmul_rn(P.theta, __fmul_rn(__uint2float_rn(u.x >> 8), s));

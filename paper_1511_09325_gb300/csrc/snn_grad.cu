@@ -395,7 +395,8 @@ int snn_grad_build(snn_net* net, int64_t n_steps, int32_t checkpoint_every, int3
   if (!out) return fail_global(SNN_EINVAL, "out is NULL");
   *out = nullptr;
   NetView v{};
-  if (!net || net_view(net, &v) != SNN_OK) return fail_global(SNN_EINVAL, "net is NULL");
+  if (!net || net_view(net, &v) != SNN_OK)
+    return fail_global(SNN_EINVAL, "net is NULL or a shard");
   if (v.precision != SNN_EXACT_F32W)
     return fail_global(SNN_EINVAL, "the differentiable form needs an SNN_EXACT_F32W net");
   if (n_steps < 1 || n_steps > (1LL << 31)) return fail_global(SNN_EINVAL, "n_steps must be >= 1");

@@ -112,6 +112,42 @@ struct Ctl {
 
 // Status codes a kernel leaves in Ctl::status (and the mapped host word).
 constexpr unsigned kStatusCounts = 1u;  // item counts disagree with the spike lists
+constexpr unsigned kStatusIngest = 2u;  // a shard received an index it cannot list
+
+// A shard: a net over a local grid E of W x H columns (its own columns and a
+// halo of stencil_radius columns around them, clipped to the global grid)
+// whose local column (lx, ly) is global column ((ex0 + lx) mod GW,
+// (ey0 + ly) mod GH).  Only the columns of T = [tx0, tx0 + tw) x [ty0, ty0 +
+// th) (local coordinates) are its own: it updates their neurons and keeps the
+// synapses that end in them; the halo's spikes arrive from other shards.
+// Random draws and spike records use global neuron indices.  A whole network
+// is the shard with on = 0 (E = T = the grid).
+struct ShardGeo {
+  int on;
+  int GW, GH;
+  int ex0, ey0;
+  int tx0, ty0, tw, th;
+};
+
+// Global column of local column (lx, ly).
+__host__ __device__ inline void shard_global_col(const ShardGeo& g, int lx, int ly, int* gx,
+                                                 int* gy) {
+  if (!g.on) {
+    *gx = lx;
+    *gy = ly;
+    return;
+  }
+  *gx = (g.ex0 + lx) % g.GW;
+  *gy = (g.ey0 + ly) % g.GH;
+}
+
+// Whether global column (gx, gy) is one of the shard's own columns.
+__host__ __device__ inline bool shard_owns_global(const ShardGeo& g, int W, int H, int gx, int gy) {
+  if (!g.on) return true;
+  const int lx = ((gx - g.ex0) % g.GW + g.GW) % g.GW;
+  const int ly = ((gy - g.ey0) % g.GH + g.GH) % g.GH;
+  return lx < W && ly < H && lx >= g.tx0 && lx < g.tx0 + g.tw && ly >= g.ty0 && ly < g.ty0 + g.th;
+}
 
 // Everything a step kernel needs, passed by value (constant bank).
 struct StepParams {
@@ -156,6 +192,7 @@ struct StepParams {
   unsigned long long* spk_part;  // spike partial sums, one per update block
   const uint32_t* deg;           // out-degree per neuron (paper law), else null
   unsigned long long* syn_part;  // synaptic events of the spikes, one per update block
+  ShardGeo sg;                   // shard geometry (sg.on = 0: a whole network)
 };
 
 // A batch of nets advanced by one persistent launch (snn_batch_*).
@@ -188,6 +225,7 @@ struct BuildParams {
   int8_t poff_dx[kMaxOff], poff_dy[kMaxOff];
   uint32_t* deg;          // [N] out-degree of each neuron
   unsigned* max_units;    // largest row, in units of 8 slots
+  ShardGeo sg;            // shard geometry (sg.on = 0: a whole network)
 };
 
 // What the differentiable form reads of a net (snn_api.cu fills it).
@@ -239,6 +277,9 @@ size_t batch_smem(size_t max_deliver_smem);
 int batch_grid(int precision, int infl, int num_sms, size_t smem);
 cudaError_t launch_batch(const BatchParams& b, int precision, int infl, int grid, size_t smem,
                          cudaStream_t st);
+// Shard: list the received spikes (global indices ids[0 .. n)) of the halo
+// columns in the step's lists, as the update kernel lists its own.
+cudaError_t launch_ingest(const StepParams& p, const uint32_t* ids, long long n, cudaStream_t st);
 cudaError_t launch_sum_parts(const unsigned long long* part, int n, unsigned long long* out,
                              cudaStream_t st);
 

@@ -164,7 +164,11 @@ struct UpdateSmem {
 // size must be the same every step.  Each spike goes to the step's list
 // (column c's part when P.ccnt is set, else one compact list) -- as a
 // descriptor when P.desc is set, else as its id -- and to the body's record
-// region as (step << 32 | id).
+// region as (step << 32 | id).  A shard (SHARD, P.sg.on) updates its own
+// columns only, draws the external input with global neuron indices and
+// records global indices; the halo's columns take part in the count
+// bookkeeping.
+template <bool SHARD>
 __device__ __forceinline__ void update_body(const StepParams& P, long long t, int vb, int vgrid,
                                             UpdateSmem& S, int tid, int bar) {
   body_sync(bar);  // the shared memory may still be read by a previous body
@@ -234,8 +238,19 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
     const long long i0 = q * 4;
     unsigned rank[4] = {0u, 0u, 0u, 0u};
     int scol[4] = {-1, -1, -1, -1};
-    if (i0 < P.N) {
-      const uint4 x = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)t, kTagExt, 0u), P.seed_lo, P.seed_hi);
+    uint32_t gq = (uint32_t)q;  // global quad of the four neurons
+    bool own = true;
+    if (SHARD && i0 < P.N) {
+      const int c = (int)((uint32_t)i0 / (uint32_t)P.npc);
+      const int l0 = (int)((uint32_t)i0 - (uint32_t)c * (uint32_t)P.npc);
+      const int cy = c / P.W, cx = c - cy * P.W;
+      own = cx >= P.sg.tx0 && cx < P.sg.tx0 + P.sg.tw && cy >= P.sg.ty0 && cy < P.sg.ty0 + P.sg.th;
+      int gx, gy;
+      shard_global_col(P.sg, cx, cy, &gx, &gy);
+      gq = (((uint32_t)gy * (uint32_t)P.sg.GW + (uint32_t)gx) * (uint32_t)P.npc + (uint32_t)l0) >> 2;
+    }
+    if (i0 < P.N && own) {
+      const uint4 x = philox4x32_10(make_uint4(gq, (uint32_t)t, kTagExt, 0u), P.seed_lo, P.seed_hi);
       reinterpret_cast<int4*>(P.acc)[q] = make_int4(0, 0, 0, 0);
       const float vin[4] = {v4.x, v4.y, v4.z, v4.w};
       const float cin[4] = {c4.x, c4.y, c4.z, c4.w};
@@ -327,7 +342,8 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
         }
         syn += P.deg != nullptr ? P.deg[id] : (uint32_t)P.K;
         const unsigned long long ri = rc + S.tpos[k] + off;
-        if ((long long)ri < P.rec_region) region[ri] = ((unsigned long long)(unsigned)t << 32) | id;
+        const uint32_t gid = SHARD ? gq * 4u + (uint32_t)e : id;
+        if ((long long)ri < P.rec_region) region[ri] = ((unsigned long long)(unsigned)t << 32) | gid;
       }
     }
     for (int k = tid; k < ncols; k += kUpdateThreads) {
@@ -362,9 +378,10 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
   }
 }
 
+template <bool SHARD>
 __global__ void __launch_bounds__(kUpdateThreads, 4) update_kernel(const StepParams P) {
   __shared__ UpdateSmem S;
-  update_body(P, P.ctl->t, (int)blockIdx.x, (int)gridDim.x, S, (int)threadIdx.x, 0);
+  update_body<SHARD>(P, P.ctl->t, (int)blockIdx.x, (int)gridDim.x, S, (int)threadIdx.x, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1070,7 +1087,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchPara
       for (int w = stid; w < kParamWords; w += kUpdateThreads)
         reinterpret_cast<uint32_t*>(&s_p[sub])[w] = reinterpret_cast<const uint32_t*>(B.nets + k)[w];
       body_sync(1 + sub);
-      update_body(s_p[sub], t, g - s_uf[k], s_uf[k + 1] - s_uf[k], SU[sub], stid, 1 + sub);
+      update_body<false>(s_p[sub], t, g - s_uf[k], s_uf[k + 1] - s_uf[k], SU[sub], stid, 1 + sub);
     }
     if (!grid_barrier(B, &s_ok)) return;
     for (int g = blockIdx.x; g < total_d; g += gridDim.x) {
@@ -1185,6 +1202,57 @@ __global__ void __launch_bounds__(256) drain_records_kernel(
   }
 }
 
+// Shard: the received spikes of step t (global indices ids[0 .. n)) that
+// belong to halo columns join the step's per-column lists as the update
+// kernel's own spikes do -- a descriptor {local index, bucket ends} at the
+// next position of the column's list and, with d_min = 1, one more item for
+// the column in this step's delivery (with d_min >= 2 the update kernel of
+// step t + d_min - 1 moves the column's count in).  Indices of the shard's
+// own columns and of columns outside its local grid are skipped.  An index
+// beyond the global network, or more than n_per_col spikes for one column
+// (a duplicated index), is skipped and sets the status word.
+__global__ void __launch_bounds__(256) ingest_kernel(const StepParams P, const uint32_t* ids,
+                                                     long long n) {
+  const long long t = P.ctl->t;
+  const long long slot = t % P.nslot;
+  const unsigned long long ng = (unsigned long long)P.sg.GW * (unsigned long long)P.sg.GH *
+                                (unsigned long long)P.npc;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const uint32_t g = ids[k];
+    if ((unsigned long long)g >= ng) {
+      set_status(P, kStatusIngest);
+      continue;
+    }
+    const uint32_t gc = g / (uint32_t)P.npc;
+    const uint32_t l = g - gc * (uint32_t)P.npc;
+    const int gy = (int)(gc / (uint32_t)P.sg.GW), gx = (int)gc - gy * P.sg.GW;
+    const int lx = wrap(gx - P.sg.ex0, P.sg.GW), ly = wrap(gy - P.sg.ey0, P.sg.GH);
+    if (lx >= P.W || ly >= P.H) continue;  // not in the local grid
+    if (lx >= P.sg.tx0 && lx < P.sg.tx0 + P.sg.tw && ly >= P.sg.ty0 && ly < P.sg.ty0 + P.sg.th)
+      continue;  // an own column: listed by the update kernel
+    const int c = ly * P.W + lx;
+    const unsigned r = atomicAdd(P.ccnt + slot * P.ncol + c, 1u);
+    if (r >= (unsigned)P.npc) {
+      set_status(P, kStatusIngest);
+      continue;
+    }
+    const uint32_t id = (uint32_t)c * (uint32_t)P.npc + l;
+    uint4* d = reinterpret_cast<uint4*>(
+        P.desc + ((long long)slot * P.N + (long long)c * P.npc + r) * P.desc_words);
+    const uint4* be = reinterpret_cast<const uint4*>(P.bend + (long long)id * kBendStride);
+    const uint4 a = be[0], b = be[1];
+    d[0] = make_uint4(id, a.x, a.y, a.z);
+    d[1] = make_uint4(a.w, b.x, b.y, b.z);
+    if (P.desc_words == 16) d[2] = make_uint4(b.w, 0u, 0u, 0u);
+    if (P.dmin == 1) {
+      const unsigned v = P.colv[c];
+      atomicAdd(P.isum + v, 1u);
+      atomicAdd(P.gsum + (v >> 5), 1u);
+    }
+  }
+}
+
 // Sum of the per-block spike counts (measurement helper).
 __global__ void sum_parts_kernel(const unsigned long long* part, int n, unsigned long long* out) {
   unsigned long long s = 0ull;
@@ -1198,7 +1266,7 @@ __global__ void sum_parts_kernel(const unsigned long long* part, int n, unsigned
 
 int update_grid(long long N, int num_sms) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, update_kernel, kUpdateThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, update_kernel<false>, kUpdateThreads, 0);
   if (per_sm < 1) per_sm = 1;
   const long long tiles = ((N + 3) / 4 + kUpdateThreads - 1) / kUpdateThreads;
   const long long g = (long long)per_sm * num_sms;
@@ -1206,7 +1274,17 @@ int update_grid(long long N, int num_sms) {
 }
 
 cudaError_t launch_update(const StepParams& p, int grid, cudaStream_t st) {
-  update_kernel<<<grid, kUpdateThreads, 0, st>>>(p);
+  if (p.sg.on)
+    update_kernel<true><<<grid, kUpdateThreads, 0, st>>>(p);
+  else
+    update_kernel<false><<<grid, kUpdateThreads, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ingest(const StepParams& p, const uint32_t* ids, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long blocks = (n + 255) / 256;
+  ingest_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(p, ids, n);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ EXPORTS = ("snn_build", "snn_step", "snn_read_spikes", "snn_pending_spikes",
            "snn_set_record_capacity", "snn_read_rates", "snn_stats", "snn_get_state",
            "snn_read_synapses", "snn_row_lengths", "snn_info", "snn_step_profiled", "snn_update_noalloc",
            "snn_debug_offset_count",
+           "snn_build_shard", "snn_shard_update", "snn_shard_deliver", "snn_shard_info",
            "snn_batch_build", "snn_batch_step", "snn_batch_net", "snn_batch_tune",
            "snn_batch_set_wait", "snn_batch_last_error", "snn_batch_destroy",
            "snn_grad_build", "snn_grad_run", "snn_grad_last_error", "snn_grad_destroy",
@@ -71,6 +72,11 @@ def load(path=LIB_PATH):
     L.snn_build.argtypes = [i32, i32, P(NeuronParams), P(SynapseParams), ctypes.c_uint64,
                             i32, vp, P(vp)]
     L.snn_step.argtypes = [vp, i64]
+    L.snn_build_shard.argtypes = [i32, i32, i32, i32, i32, i32, P(NeuronParams),
+                                  P(SynapseParams), ctypes.c_uint64, i32, vp, P(vp)]
+    L.snn_shard_update.argtypes = [vp]
+    L.snn_shard_deliver.argtypes = [vp, vp, i64, ctypes.c_int32]
+    L.snn_shard_info.argtypes = [vp, vp, i32]
     L.snn_read_spikes.argtypes = [vp, vp, vp, i64, P(i64)]
     L.snn_pending_spikes.argtypes = [vp, P(i64)]
     L.snn_set_record_capacity.argtypes = [vp, i64]
@@ -155,6 +161,47 @@ def snn_build(grid_w, grid_h, neuron, synapse, seed, precision, stream=None):
 
 def snn_step(handle, n_steps):
     _check(load().snn_step(handle, int(n_steps)), handle)
+
+
+def snn_build_shard(grid_w, grid_h, x0, y0, w, h, neuron, synapse, seed, precision,
+                    stream=None):
+    """Build the shard of tile (x0, y0, w, h); returns the opaque handle."""
+    L = load()
+    hd = ctypes.c_void_p()
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    n = neuron_struct(neuron)
+    s = synapse_struct(synapse)
+    rc = L.snn_build_shard(int(grid_w), int(grid_h), int(x0), int(y0), int(w), int(h),
+                           ctypes.byref(n), ctypes.byref(s), int(seed), prec, stream,
+                           ctypes.byref(hd))
+    _check(rc, None)
+    return hd.value
+
+
+def snn_shard_update(handle):
+    _check(load().snn_shard_update(handle), handle)
+
+
+def snn_shard_deliver(handle, ids):
+    """Deliver step t with the received global spike indices `ids`: a numpy
+    int32 array (host) or a contiguous int32 CUDA tensor (device; it must
+    stay unchanged until the net's stream has passed the delivery)."""
+    if hasattr(ids, "is_cuda") and ids.is_cuda:
+        import torch
+        if ids.dtype != torch.int32 or not ids.is_contiguous():
+            raise TypeError("device ids must be a contiguous int32 tensor")
+        rc = load().snn_shard_deliver(handle, ctypes.c_void_p(ids.data_ptr()), int(ids.numel()), 1)
+    else:
+        a = np.ascontiguousarray(np.asarray(ids, dtype=np.int32))
+        rc = load().snn_shard_deliver(handle, _p(a), int(a.size), 0)
+    _check(rc, handle)
+
+
+def snn_shard_info(handle):
+    g = np.zeros(10, np.int32)
+    _check(load().snn_shard_info(handle, _p(g), 10), handle)
+    keys = ("grid_w", "grid_h", "local_w", "local_h", "ex0", "ey0", "tx0", "ty0", "w", "h")
+    return {k: int(v) for k, v in zip(keys, g)}
 
 
 def snn_pending_spikes(handle):
@@ -493,6 +540,132 @@ class Net:
 
     def step_profiled(self, n_steps):
         return snn_step_profiled(self.handle, n_steps)
+
+    def close(self):
+        if self.handle:
+            snn_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def split_grid(grid_w, grid_h, nx, ny):
+    """Tiles (x0, y0, w, h) of an nx x ny partition of a grid_w x grid_h grid,
+    row-major; tile sides differ by at most one column."""
+    if not (1 <= nx <= grid_w and 1 <= ny <= grid_h):
+        raise ValueError("need 1 <= nx <= grid_w and 1 <= ny <= grid_h")
+    xs = [grid_w * i // nx for i in range(nx + 1)]
+    ys = [grid_h * j // ny for j in range(ny + 1)]
+    return [(xs[i], ys[j], xs[i + 1] - xs[i], ys[j + 1] - ys[j])
+            for j in range(ny) for i in range(nx)]
+
+
+def shard_layout(world_size, grid_w, grid_h):
+    """nx x ny for world_size shards: the factorisation whose tiles are the
+    most nearly square (least halo per tile)."""
+    best = None
+    for nx in range(1, world_size + 1):
+        if world_size % nx:
+            continue
+        ny = world_size // nx
+        if nx > grid_w or ny > grid_h:
+            continue
+        cost = grid_w / nx + grid_h / ny  # half the perimeter of a tile
+        if best is None or cost < best[0]:
+            best = (cost, nx, ny)
+    if best is None:
+        raise ValueError("cannot split a %dx%d grid into %d tiles" % (grid_w, grid_h, world_size))
+    return best[1], best[2]
+
+
+def exchange_spikes(ids, group=None):
+    """All-gather of every rank's spike indices of one step over
+    torch.distributed: the ranks' counts first, then the id lists padded to
+    the largest count.  `ids` is an int32 tensor (CPU for gloo, CUDA for
+    NCCL); returns the concatenation over all ranks (rank order)."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size(group)
+    n = torch.tensor([ids.numel()], dtype=torch.int64, device=ids.device)
+    counts = [torch.zeros_like(n) for _ in range(ws)]
+    dist.all_gather(counts, n, group=group)
+    counts = [int(c.item()) for c in counts]
+    m = max(counts)
+    if m == 0:
+        return ids.new_zeros(0)
+    buf = ids.new_zeros(m)
+    buf[:ids.numel()] = ids
+    parts = [ids.new_zeros(m) for _ in range(ws)]
+    dist.all_gather(parts, buf, group=group)
+    return torch.cat([p[:c] for p, c in zip(parts, counts)])
+
+
+class Shard:
+    """The part of a grid_w x grid_h network that one process holds: tile
+    (x0, y0, w, h) and the halo rows that target it.  A step is
+    update() -> spikes() -> exchange -> deliver(received)."""
+
+    def __init__(self, grid_w, grid_h, tile, neuron, synapse, seed, precision="f32w",
+                 stream=None):
+        x0, y0, w, h = tile
+        self.tile = (int(x0), int(y0), int(w), int(h))
+        self.neuron, self.synapse = dict(neuron), dict(synapse)
+        self.npc = neuron["n_per_col"]
+        self.handle = snn_build_shard(grid_w, grid_h, x0, y0, w, h, neuron, synapse, seed,
+                                      precision, stream)
+        self.geo = snn_shard_info(self.handle)
+        g = self.geo
+        self.n_cols = g["local_w"] * g["local_h"]
+        self.n = self.n_cols * self.npc
+
+    def local_to_global(self, local_ids):
+        """Global neuron indices of local neuron indices."""
+        g = self.geo
+        j = np.asarray(local_ids, np.int64)
+        c, l = j // self.npc, j % self.npc
+        ly, lx = c // g["local_w"], c % g["local_w"]
+        gx = (g["ex0"] + lx) % g["grid_w"]
+        gy = (g["ey0"] + ly) % g["grid_h"]
+        return (gy * g["grid_w"] + gx) * self.npc + l
+
+    def tile_local_neurons(self):
+        """Local indices of the tile's neurons, tile row-major, then l."""
+        g = self.geo
+        ly, lx = np.meshgrid(np.arange(g["ty0"], g["ty0"] + g["h"]),
+                             np.arange(g["tx0"], g["tx0"] + g["w"]), indexing="ij")
+        c = (ly * g["local_w"] + lx).reshape(-1, 1)
+        return (c * self.npc + np.arange(self.npc)).reshape(-1)
+
+    def update(self):
+        snn_shard_update(self.handle)
+
+    def spikes(self, cap=None):
+        return snn_read_spikes(self.handle, cap)
+
+    def deliver(self, ids):
+        snn_shard_deliver(self.handle, ids)
+
+    def state(self):
+        return snn_get_state(self.handle, self.n)
+
+    def rates(self):
+        return snn_read_rates(self.handle, self.n_cols)
+
+    def stats(self):
+        return snn_stats(self.handle)
+
+    def info(self):
+        return snn_info(self.handle)
 
     def close(self):
         if self.handle:

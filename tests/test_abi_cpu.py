@@ -98,6 +98,24 @@ def test_calls_on_null_net_fail_cleanly(lib):
     assert lib.snn_row_lengths(None, 0, 1, None) == snn.SNN_EINVAL
 
 
+def test_shard_entry_points_validate_before_touching_a_device(lib):
+    n, s = W.neuron_params(), W.synapse_params()
+    # tiles outside the grid, n_per_col not a multiple of 4, the paper law:
+    # refused before any stream exists
+    for args in [(4, 2, (0, 0, 0, 1), n, s), (4, 2, (3, 0, 2, 1), n, s),
+                 (4, 2, (-1, 0, 1, 1), n, s), (4, 2, (0, 1, 1, 2), n, s),
+                 (4, 2, (0, 0, 2, 2), W.neuron_params(n_per_col=102, n_exc=80), s),
+                 (4, 2, (0, 0, 2, 2), n, W.synapse_params(connectivity=1)),
+                 (0, 2, (0, 0, 1, 1), n, s)]:
+        gw, gh, tile, nn, ss = args
+        with pytest.raises(snn.SnnError) as e:
+            snn.snn_build_shard(gw, gh, *tile, nn, ss, 1, "f32w")
+        assert e.value.code == snn.SNN_EINVAL
+    assert lib.snn_shard_update(None) == snn.SNN_EINVAL
+    assert lib.snn_shard_deliver(None, None, 0, 0) == snn.SNN_EINVAL
+    assert lib.snn_shard_info(None, None, 0) == snn.SNN_EINVAL
+
+
 def test_gradient_entry_points_refuse_null_arguments(lib):
     import ctypes
 

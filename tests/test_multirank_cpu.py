@@ -3,9 +3,11 @@
 1. The paper distributes the columns of the grid over MPI processes that
    exchange spikes every step (Sec. 2).  Here each rank owns a tile of
    columns, integrates only its own neurons (the dense restatement of the
-   step) and all-gathers the spike vector once per step (the minimum delay is
-   one step, so one exchange per step suffices); the union of the ranks'
-   rasters must equal the single-process oracle's raster bit for bit.
+   step) and all-gathers its spike index list once per step with the
+   library's exchange helper (the minimum delay is one step, so one exchange
+   per step suffices); the union of the ranks' rasters must equal the
+   single-process oracle's raster bit for bit.  The helper itself is checked
+   with uneven and empty lists, and the tiling helpers on their own.
 2. bench.py's whole-job reduction over N replicas takes the slowest rank's
    time and the sum of the ranks' events.
 """
@@ -53,11 +55,14 @@ def _partitioned_worker(rank, world, port, steps, out_dir, gw, gh):
     c0, c1 = rank * ncol // world, (rank + 1) * ncol // world
     rows = np.arange(c0 * 100, c1 * 100)
 
+    from paper_1511_09325_gb300 import snn
+
     def exchange(local):
-        mine = torch.from_numpy(local.astype(np.uint8))
-        parts = [torch.zeros_like(mine) for _ in range(world)]
-        dist.all_gather(parts, mine)
-        return np.logical_or.reduce([q.numpy().astype(bool) for q in parts])
+        mine = torch.from_numpy(np.flatnonzero(local).astype(np.int32))
+        got = snn.exchange_spikes(mine).numpy()
+        fired = np.zeros(local.size, bool)
+        fired[got] = True
+        return fired
 
     raster, v, _, _ = simulate(oracle, net, steps, rows=rows, exchange=exchange)
     np.save(os.path.join(out_dir, "raster%d.npy" % rank), np.array(raster, np.int64).reshape(-1, 2))
@@ -168,3 +173,50 @@ def test_bench_remeasure_decision_is_taken_by_all_ranks(tmp_path):
     mp.spawn(_any_rank_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
     for r in range(2):
         assert list(np.load(tmp_path / ("any%d.npy" % r))) == [True, False]
+
+
+def _exchange_worker(rank, world, port, out_dir):
+    sys.path.insert(0, ROOT)
+    import torch
+
+    from paper_1511_09325_gb300 import snn
+
+    dist = _init(rank, world, port)
+    # rank r sends r * 3 ids (rank 0 sends none), values 1000 r + k
+    mine = torch.arange(rank * 3, dtype=torch.int32) + 1000 * rank
+    got = snn.exchange_spikes(mine)
+    empty = snn.exchange_spikes(torch.zeros(0, dtype=torch.int32))
+    np.save(os.path.join(out_dir, "ex%d.npy" % rank), got.numpy())
+    assert empty.numel() == 0
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_spike_exchange_gathers_every_rank_in_order(tmp_path, world):
+    mp.spawn(_exchange_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    want = np.concatenate([np.arange(r * 3, dtype=np.int32) + 1000 * r for r in range(world)])
+    for r in range(world):
+        assert np.array_equal(np.load(tmp_path / ("ex%d.npy" % r)), want)
+
+
+def test_split_grid_covers_the_grid_once():
+    sys.path.insert(0, ROOT)
+    from paper_1511_09325_gb300 import snn
+
+    for gw, gh, nx, ny in [(4, 2, 2, 1), (9, 5, 3, 2), (96, 96, 4, 2), (7, 3, 7, 3), (1, 1, 1, 1)]:
+        tiles = snn.split_grid(gw, gh, nx, ny)
+        assert len(tiles) == nx * ny
+        cover = np.zeros((gh, gw), np.int32)
+        for x0, y0, w, h in tiles:
+            assert w >= 1 and h >= 1
+            cover[y0:y0 + h, x0:x0 + w] += 1
+        assert np.all(cover == 1)
+        ws = sorted(set(w for _, _, w, _ in tiles))
+        assert ws[-1] - ws[0] <= 1
+    with pytest.raises(ValueError):
+        snn.split_grid(2, 2, 3, 1)
+    assert snn.shard_layout(2, 96, 96) in [(2, 1), (1, 2)]
+    assert snn.shard_layout(4, 96, 96) == (2, 2)
+    assert snn.shard_layout(8, 96, 96) in [(4, 2), (2, 4)]
+    assert snn.shard_layout(2, 4, 2) == (2, 1)
+    assert snn.shard_layout(3, 1, 9) == (1, 3)
