@@ -12,6 +12,11 @@ Prints one JSON line.
 
 N > 1 runs N independent replicas (one network per GPU, seed + rank), launched
 with torch.distributed.run; rank 0 prints the whole-job line.
+--sharded runs ONE network split into N x M column tiles instead (M =
+--shards-per-gpu shards per rank, stepped in turn; the step's spike index
+lists are gathered on each rank and all-gathered over torch.distributed every
+step; with N = M = 1 the single shard holds the whole grid and nothing is
+exchanged, which times the split step's host round trip).
 --impl reference times the CPU oracle on a bounded sample of the workload.
 """
 import argparse
@@ -47,6 +52,10 @@ def _args():
                     help="steps of the per-kernel timing pass (default: all timed steps)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--sharded", action="store_true",
+                    help="one network split into column tiles over the ranks")
+    ap.add_argument("--shards-per-gpu", type=int, default=1,
+                    help="--sharded: tiles each rank holds (stepped in turn on its GPU)")
     return ap.parse_args()
 
 
@@ -744,10 +753,151 @@ def _paper_form(snn, torch, stream, warmup, steps=2000):
             "update_gbs": kb[0] / (kms[0] * 1e-3) / 1e9}
 
 
+def run_sharded(args):
+    """One network of the workload split into column tiles, M per rank.  A
+    step: update of every own tile, drain of their spike records (global
+    indices, device -> host), the concatenated lists all-gathered over the
+    ranks (one rank: nothing to send), delivery of the received spikes into
+    each tile.  Timed on the host clock (the step waits for the exchange)
+    with a barrier and a device sync on both sides; value = synaptic events
+    of all ranks / the slowest rank's time."""
+    import numpy as np
+    import torch
+
+    from paper_1511_09325_gb300 import build as B
+    from paper_1511_09325_gb300 import snn
+
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    snn.load()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    uuid = str(getattr(props, "uuid", "") or "")
+    if uuid and not uuid.startswith("GPU-"):
+        uuid = "GPU-" + uuid
+    cfg = W.WORKLOADS[args.workload]
+    n, s = W.neuron_params(), W.synapse_params(**cfg.get("synapse", {}))
+    M = max(1, args.shards_per_gpu)
+    nx, ny = snn.shard_layout(ws * M, cfg["grid_w"], cfg["grid_h"])
+    tiles = snn.split_grid(cfg["grid_w"], cfg["grid_h"], nx, ny)[rank * M:(rank + 1) * M]
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    shards = [snn.Shard(cfg["grid_w"], cfg["grid_h"], t, n, s, cfg["seed"], cfg["precision"],
+                        stream=stream.cuda_stream) for t in tiles]
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    nbytes = {"h2d": 0, "d2h": 0}
+    alone = ws == 1 and M == 1
+
+    def step():
+        for sh in shards:
+            sh.update()
+        mine = []
+        for sh in shards:
+            _, ids, over = sh.spikes()
+            if over:
+                raise RuntimeError("spike records dropped")
+            nbytes["d2h"] += 8 * ids.size + 16
+            mine.append(ids.astype(np.int32))
+        if alone:
+            shards[0].deliver(np.zeros(0, np.int32))
+            return
+        mine = np.concatenate(mine)
+        if dist:
+            with torch.cuda.stream(stream):
+                dev = torch.from_numpy(mine).to("cuda")
+                got = snn.exchange_spikes(dev)
+            nbytes["h2d"] += 4 * mine.size
+            for sh in shards:
+                sh.deliver(got)
+        else:
+            nbytes["h2d"] += 4 * mine.size * len(shards)
+            for sh in shards:
+                sh.deliver(mine)
+
+    def stats():
+        r = e = 0.0
+        for sh in shards:
+            a, b, _ = sh.stats()
+            r += a
+            e += b
+        return r, e
+
+    K, Wm, S = args.steps, args.warmup, args.settle
+    for _ in range(S + Wm):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(uuid)
+    clocks.start()
+    r0, e0 = stats()
+    nbytes["h2d"] = nbytes["d2h"] = 0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = (time.perf_counter() - t0) * 1e3
+    clk = clocks.stop()
+    if clk is not None:
+        clk["rejected"] = bool(clocks_rejected(clk))
+    r1, e1 = stats()
+    rec_ev, ext_ev = r1 - r0, e1 - e0
+    own_ms = ms
+    if dist:
+        ms, rec_ev, ext_ev = reduce_ranks(dist, ms, rec_ev, ext_ev, "cuda")
+    kept = sum(sh.info()["synapses"] for sh in shards)
+    geo = [[sh.geo["local_w"], sh.geo["local_h"]] for sh in shards]
+    for sh in shards:
+        sh.close()
+    if rank == 0:
+        value = rec_ev / (ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+            "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "mode": "sharded",
+            "dtype": "f32+i32" if cfg["precision"] == "f32w" else "f16+i32",
+            "data": "synthetic",
+            "config": dict(_config(args, cfg, None, ws), parallelism="tiles%dx%d" % (nx, ny),
+                           shards_per_gpu=M,
+                           exchange=("all-gather of spike index lists" if dist else
+                                     "host concatenation" if not alone else "none (1 shard)")),
+            "rank0": {"tiles": [list(t) for t in tiles], "local_grids": geo,
+                      "synapses_kept": kept, "ms": own_ms},
+            "build_s": build_s,
+            # per shard: update, record drain, ingest of the received list
+            # (when one is sent), delivery
+            "gpu_launches": (3 if alone else 4) * M * K,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": nbytes["h2d"] / K,
+                    "d2h_bytes_per_step": nbytes["d2h"] / K,
+                    "note": "the sharded step itself crosses the host every step"},
+            "roofline": None,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sharded:
+        run_sharded(args)
     else:
         run_ours(args)
 
