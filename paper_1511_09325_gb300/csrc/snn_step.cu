@@ -712,6 +712,31 @@ __device__ __forceinline__ void stream_items(const StepParams& P, const Item& it
   }
 }
 
+// Adds the window's `slots` columns (n_per_col = npc words each, npc a
+// multiple of 4) into the accumulator with one bulk asynchronous reduction
+// (cp.reduce.async.bulk .add.s32, element-wise atomic in L2) per column,
+// issued by threads 0 .. slots - 1.  The shared-memory writes of every thread
+// are made visible to the bulk copies (async-proxy fence, then a barrier);
+// the issuing threads wait until their copies have read the window, and a
+// last barrier hands the window back to the block.
+__device__ __forceinline__ void flush_window_bulk(const DeliverSmem& S, uint32_t win_s, int slots,
+                                                  int npc, int32_t* acc, int tid) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (tid < slots) {
+    const uint32_t bytes = (uint32_t)npc * 4u;
+    const uint32_t src = win_s + (uint32_t)tid * bytes;
+    int32_t* dst = acc + S.wbase[tid];
+    asm volatile(
+        "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.s32 [%0], [%1], %2;\n\t"
+        "cp.async.bulk.commit_group;\n\t"
+        "cp.async.bulk.wait_group.read 0;" ::"l"(dst),
+        "r"(src), "r"(bytes)
+        : "memory");
+  }
+  __syncthreads();
+}
+
 // Delivery block vb of vgrid (NT threads) for step t.  The step's items,
 // ordered by (virtual column, delay bucket, spiker), are split into at most
 // vgrid equal contiguous ranges of at least P.min_items items; block vb
@@ -948,22 +973,35 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
         k0 = k1;
       }
     }
-    __syncthreads();
-    // flush the window with coalesced reductions, leaving it zeroed: word
-    // m is neuron l of slot s; (s, l) advance with m
     const uint32_t wlen = (uint32_t)(wg.ww * wg.wh) * (uint32_t)P.npc;
-    uint32_t fs = div_by((uint32_t)tid, (uint32_t)P.npc, P.npc_m);
-    uint32_t fl = (uint32_t)tid - fs * (uint32_t)P.npc;
-    for (uint32_t m = tid; m < wlen; m += NT) {
-      const int32_t x = win[m];
-      if (x) {
-        red_add(P.acc + S.wbase[fs] + fl, x, pol);
-        win[m] = 0;
+    if ((P.npc & 3) == 0) {
+      // bulk flush: each window slot (one column, n_per_col words, 16-byte
+      // aligned in both memories) is added into the accumulator by one
+      // asynchronous bulk reduction; the window is cleared once the bulk
+      // copies have read it (unless no part follows in this body)
+      flush_window_bulk(S, win_s, wg.ww * wg.wh, P.npc, P.acc, tid);
+      if (ve + 1 <= v1) {
+        for (uint32_t i = tid; i < (wlen >> 2); i += NT) reinterpret_cast<int4*>(win)[i] = make_int4(0, 0, 0, 0);
+      } else {
+        win_zero = false;
       }
-      fl += NT;
-      while (fl >= (uint32_t)P.npc) {
-        fl -= (uint32_t)P.npc;
-        ++fs;
+    } else {
+      __syncthreads();
+      // flush the window with coalesced reductions, leaving it zeroed: word
+      // m is neuron l of slot s; (s, l) advance with m
+      uint32_t fs = div_by((uint32_t)tid, (uint32_t)P.npc, P.npc_m);
+      uint32_t fl = (uint32_t)tid - fs * (uint32_t)P.npc;
+      for (uint32_t m = tid; m < wlen; m += NT) {
+        const int32_t x = win[m];
+        if (x) {
+          red_add(P.acc + S.wbase[fs] + fl, x, pol);
+          win[m] = 0;
+        }
+        fl += NT;
+        while (fl >= (uint32_t)P.npc) {
+          fl -= (uint32_t)P.npc;
+          ++fs;
+        }
       }
     }
     if (tid == 0) S.next = 0u;
