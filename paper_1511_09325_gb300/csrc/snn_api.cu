@@ -19,10 +19,12 @@ struct snn_net {
   int precision = 0, rowcap = 0, rec_size = 0, num_sms = 0, update_grid = 0;
   bool agg = true;
   int deliver_grid = 0;
-  int tile = 1, ring = 1, win_cap = 0, desc_words = 8;  // delivery tiles and windows
+  int tile = 1, ring = 0, win_cap = 0, desc_words = 8;  // delivery tiles and windows
   int part_cols = kMaxTileCols;
   size_t window_budget = 0;  // bytes of shared memory a delivery window may take
   unsigned min_items = 256;  // fewest items a delivery block takes
+  unsigned win_items = kWinMinItems;  // fewest items of a windowed tile part
+  unsigned cost_win = kCostWin, cost_part = kCostPart;  // range split's fixed costs
   long long N = 0, Npad = 0, ncol = 0;
   uint64_t seed = 0;
   snn_neuron_params neuron{};
@@ -220,9 +222,14 @@ uint32_t recip32(uint32_t d) {
 }
 
 // Delivery tiles: the largest square tile (side <= kMaxTile) whose window --
-// the tile plus a ring of one column, clipped to the grid -- fits the shared
-// memory budget of a delivery block: one block per SM for a net of its own,
-// two per SM in the batch kernel.
+// the tile plus a ring of kWindowRing columns, clipped to the grid -- fits the
+// shared memory budget of a delivery block: one block per SM for a net of its
+// own, two per SM in the batch kernel.  Measured at 96x96 (FP16, Down, middle
+// and Up states): a 6x6 tile without ring (80 % of the synapses land in the
+// window, each column is flushed once per part) beats a 4x4 tile with a ring
+// of one (88 %, but 36 window columns flushed per 16 columns of spikes) by
+// 13 %, 17 % and 3 %; 5x5 and 4x4 tiles without ring and 3x3 with a ring are
+// slower still.
 constexpr size_t kWindowBudget = 196 * 1024;
 constexpr size_t kBatchWindowBudget = 96 * 1024;
 // Fewest items a delivery block takes (fewer blocks run when a step has few
@@ -235,9 +242,10 @@ constexpr unsigned kBatchMinItems = 256;
 // of shared memory beside the window.
 constexpr int kPartCols = kMaxTileCols;
 constexpr int kBatchPartCols = 16;
+constexpr int kWindowRing = 0;
 
 void choose_tiles(snn_net* net) {
-  net->ring = 1;
+  net->ring = kWindowRing;
   int t = std::min(kMaxTile, std::max(net->W, net->H));
   for (; t > 1; --t) {
     const size_t ww = (size_t)std::min(t + 2 * net->ring, net->W);
@@ -323,6 +331,9 @@ void fill_step_params(snn_net* net) {
   p.win_cap = net->win_cap;
   p.desc_words = net->desc_words;
   p.min_items = net->min_items;
+  p.win_items = net->win_items;
+  p.cost_win = net->cost_win;
+  p.cost_part = net->cost_part;
   p.npc_m = recip32((uint32_t)net->npc);
   p.w_m = recip32((uint32_t)net->W);
   p.seed_lo = (uint32_t)(net->seed & 0xFFFFFFFFu);

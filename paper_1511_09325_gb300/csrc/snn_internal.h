@@ -72,6 +72,12 @@ constexpr int kCenterCode = (3 << 3) | 3;
 constexpr int kMaxGridSide = 16383;     // columns per grid side (14-bit coordinates)
 constexpr int kMaxTile = 8;             // delivery tile side, columns
 constexpr int kMaxTileCols = kMaxTile * kMaxTile;
+constexpr unsigned kWinMinItems = 512;  // default fewest items of a windowed tile part
+// Fixed costs, in items, that the delivery's range split adds to a group of
+// 32 columns with at least kWinMinItems items (window set-up and flush) and
+// to one with fewer but some items (table set-up).
+constexpr unsigned kCostWin = 1024;
+constexpr unsigned kCostPart = 256;
 
 // Tables computed on the host in FP64 and rounded once.
 struct HostTables {
@@ -160,6 +166,8 @@ struct StepParams {
   int win_cap;             // ints of the window (largest tile window)
   int desc_words;          // u32 words per spike descriptor (8 or 16)
   unsigned min_items;      // fewest items a delivery block takes (fewer blocks run)
+  unsigned win_items;      // fewest items of a tile part that uses the window
+  unsigned cost_win, cost_part;  // fixed cost (in items) of a windowed / other group
   uint32_t npc_m, w_m;     // floor(2^32 / n_per_col), floor(2^32 / W) (capped)
   uint32_t seed_lo, seed_hi;
   float theta, vr, dc, pvv, pcc, pvc_e, pvc_i;

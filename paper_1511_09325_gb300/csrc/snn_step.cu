@@ -19,20 +19,22 @@
 //   receives additions, not a d_max-slot ring.  The (delay bucket, spiker)
 //   items of the last d_max steps, ordered by (virtual column, bucket,
 //   spiker), form one virtual list split evenly over a persistent grid of one
-//   1024-thread block per SM.  Virtual columns run tile by tile (tiles of
-//   tile x tile columns), so a block's items come from a compact patch of the
-//   grid.  For each tile part with enough items, a block keeps a
-//   shared-memory window over the tile's columns and a ring of one column
-//   around them -- where about seven eighths of the tile's synapses land (the
-//   local half and most of the near stencil) -- sums those synapses there
-//   with shared-memory reductions and flushes the window once into the
-//   accumulator; the other synapses go to L2 as fire-and-forget int32
-//   reductions.  A warp takes batches of 32 items: lane e resolves item e (a
-//   binary search in the tile part's table of (column, bucket) counts and one
-//   descriptor load) and streams that bucket by itself, 32-byte sectors
-//   double-buffered in registers; the next batch is resolved before the
-//   current one is streamed.  Integer addition makes the result independent
-//   of the order.  The last block to finish advances the step counter.
+//   768-thread block per SM.  Virtual columns run tile by tile (tiles of
+//   tile x tile columns, 6 x 6 at n_per_col = 1240), so a block's items come
+//   from a compact patch of the grid.  For each tile part with enough items,
+//   a block keeps a shared-memory window over the tile's columns (and a ring
+//   of P.ring columns around them) -- where about four fifths of the tile's
+//   synapses land (the local half and most of the near stencil) -- sums
+//   those synapses there with shared-memory reductions and flushes the window
+//   once into the accumulator by bulk asynchronous reductions; the other
+//   synapses go to L2 as fire-and-forget int32 reductions.  A warp takes
+//   batches of 32 items: lane e resolves item e (a binary search in the tile
+//   part's table of (column, bucket) counts and one descriptor load); the
+//   batch's buckets are then streamed as one list of 32-byte sectors dealt to
+//   the lanes in balanced rounds, two rounds in flight, and the next batch is
+//   resolved before the current one is streamed.  Integer addition makes the
+//   result independent of the order.  The last block to finish advances the
+//   step counter.
 #include <algorithm>
 
 #include "snn_device.cuh"
@@ -50,7 +52,6 @@ constexpr int kDepthF16 = 2;     // the same, F16W
 constexpr int kTile = kUpdateThreads * 4;    // neurons per update tile
 constexpr int kTileCols = kTile / 2 + 2;     // columns a tile can touch (npc >= 2)
 constexpr int kBatchItems = 32;              // items per warp batch (one per lane)
-constexpr unsigned kWinMinItems = 512;       // fewest items of a tile part that uses the window
 
 struct NeuronOut {
   float v, c;
@@ -439,6 +440,7 @@ __device__ __forceinline__ WinGeo win_geo(const StepParams& P, const TileGeo& g,
 struct DeliverSmem {
   unsigned long long wsum[32];    // per-warp sums of block_scan
   unsigned long long xgp[2];      // items before the group holding lo / hi - 1
+  unsigned long long ipt[2];      // item positions of the block's range ends
   unsigned long long p0;          // items before virtual column v0
   int xg[2];                      // group holding lo / hi - 1
   int v0, v1;                     // first and last virtual column of the block's items
@@ -494,7 +496,9 @@ __device__ __forceinline__ unsigned long long block_scan(unsigned long long v, D
 // offset's target column -- its shared-window address, or bit 31 set and its
 // first neuron in the accumulator.  The entries of a sector's eight records
 // are loaded before any of them is delivered, so the loads are not ordered
-// behind the shared-memory reductions.
+// behind the shared-memory reductions.  (Measured: one reduction with a
+// generic 64-bit address instead of the two predicated ones made the
+// delivery 2.6-2.8x slower: generic atomics on shared memory are slow.)
 __device__ __forceinline__ uint32_t nb_entry(uint32_t w, uint32_t nbrow) {
   uint32_t e;
   asm volatile("ld.shared.u32 %0, [%1];" : "=r"(e) : "r"(nbrow + ((w >> 9) & 0xFCu)));
@@ -776,19 +780,53 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
     S.next = 0u;
   }
 
-  // the block's item range, from the group counts
+  // the block's item range, from the group counts.  The ranges split the
+  // step's cost evenly: a group of 32 virtual columns costs its items plus a
+  // fixed part (P.cost_win when its items reach the window threshold -- the
+  // set-up and flush of a windowed part -- else P.cost_part when it has
+  // items), laid out before the group's items; a cost point maps to the item
+  // position it falls on (the group's first item while in the fixed part).
+  // The mapping is monotone, so consecutive blocks' ranges tile the items.
   const int ngrp = (P.ncol + 31) >> 5;
   const int per = (ngrp + NT - 1) / NT;
   const int g0 = tid * per;
-  unsigned long long mine = 0ull;
-  for (int g = g0; g < g0 + per && g < ngrp; ++g) mine += P.gsum[g];
-  unsigned long long total = 0ull;
+  auto group_cost = [&](unsigned v) -> unsigned long long {
+    return (unsigned long long)v + (v >= P.win_items ? P.cost_win : (v ? P.cost_part : 0u));
+  };
+  unsigned long long mine = 0ull, mcost = 0ull;
+  for (int g = g0; g < g0 + per && g < ngrp; ++g) {
+    const unsigned v = P.gsum[g];
+    mine += v;
+    mcost += group_cost(v);
+  }
+  unsigned long long total = 0ull, ctotal = 0ull;
   const unsigned long long excl = block_scan(mine, S, &total);
+  const unsigned long long cexcl = block_scan(mcost, S, &ctotal);
   const unsigned long long want = (total + P.min_items - 1) / P.min_items;
   const int nact = (int)(want < (unsigned long long)vgrid ? (want ? want : 1ull) : (unsigned long long)vgrid);
   if (vb >= nact) return;
-  const unsigned long long lo = total * (unsigned long long)vb / (unsigned long long)nact;
-  const unsigned long long hi = total * (unsigned long long)(vb + 1) / (unsigned long long)nact;
+  for (int i = 0; i < 2; ++i) {
+    const unsigned long long x = ctotal * (unsigned long long)(vb + i) / (unsigned long long)nact;
+    if (x >= ctotal) {
+      if (tid == 0) S.ipt[i] = total;
+    } else if (x >= cexcl && x < cexcl + mcost) {
+      unsigned long long rc = cexcl, ri = excl;
+      for (int g = g0; g < g0 + per && g < ngrp; ++g) {
+        const unsigned v = P.gsum[g];
+        const unsigned long long c = group_cost(v);
+        if (x < rc + c) {
+          const unsigned long long fixed = c - v;
+          S.ipt[i] = ri + (x - rc > fixed ? x - rc - fixed : 0ull);
+          break;
+        }
+        rc += c;
+        ri += v;
+      }
+    }
+  }
+  __syncthreads();
+  const unsigned long long lo = S.ipt[0];
+  const unsigned long long hi = S.ipt[1];
   if (lo >= hi) return;
   for (int i = 0; i < 2; ++i) {
     const unsigned long long x = i == 0 ? lo : hi - 1;
@@ -857,7 +895,7 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
         const unsigned long long lo_in = pb > lo ? pb : lo;
         const unsigned long long hi_in = pb + x < hi ? pb + x : hi;
         const unsigned long long in = hi_in > lo_in ? hi_in - lo_in : 0ull;
-        if (P.agg && in >= kWinMinItems) {
+        if (P.agg && in >= P.win_items) {
           if (tiles == 0) {
             wnd = true;
             e = te + 1;
