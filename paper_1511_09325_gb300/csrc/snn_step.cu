@@ -157,6 +157,10 @@ struct UpdateSmem {
   unsigned long long rc, spk;
   unsigned long long synw[kUpdateThreads / 32];  // synaptic events per warp
   unsigned ksum[kUpdateThreads / 32];
+  // bucket ends of the tile's spikers, copied asynchronously as soon as the
+  // spike is known (slot 4 tid + e: neuron e of the thread's quad), so the
+  // load's latency overlaps the tile's count bookkeeping
+  uint4 bst[kTile][2];
 };
 
 // Update body vb of vgrid for step t, run by kUpdateThreads threads (thread
@@ -284,6 +288,20 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
           ++col;
         }
       }
+      if (P.desc != nullptr) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (scol[e] >= 0) {
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&S.bst[tid * 4 + e][0]);
+            const uint4* src = reinterpret_cast<const uint4*>(P.bend + (i0 + e) * kBendStride);
+            asm volatile(
+                "cp.async.cg.shared.global [%0], [%1], 16;\n\t"
+                "cp.async.cg.shared.global [%2], [%3], 16;" ::"r"(dst),
+                "l"(src), "r"(dst + 16u), "l"(src + 1)
+                : "memory");
+          }
+        }
+      }
       reinterpret_cast<float4*>(P.V)[q] = make_float4(vout[0], vout[1], vout[2], vout[3]);
       reinterpret_cast<float4*>(P.C)[q] = make_float4(cout[0], cout[1], cout[2], cout[3]);
       reinterpret_cast<uchar4*>(P.R)[q] = make_uchar4((unsigned char)rout[0], (unsigned char)rout[1],
@@ -322,6 +340,7 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
     }
     body_sync(bar);
     const unsigned long long rc = S.rbase;
+    if (P.desc != nullptr) asm volatile("cp.async.wait_all;" ::: "memory");
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if (scol[e] >= 0) {
@@ -331,10 +350,9 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
         const uint32_t id = (uint32_t)(i0 + e);
         const long long pos = P.ccnt != nullptr ? S.lbase[k] + off : S.cbase + S.tpos[k] + off;
         if (P.desc != nullptr) {
-          // descriptor: id, then the bucket ends of the spiker's row
+          // descriptor: id, then the bucket ends of the spiker's row (staged)
           uint4* d = reinterpret_cast<uint4*>(P.desc + ((long long)slot * P.N + pos) * P.desc_words);
-          const uint4* be = reinterpret_cast<const uint4*>(P.bend + (long long)id * kBendStride);
-          const uint4 a = be[0], b = be[1];
+          const uint4 a = S.bst[tid * 4 + e][0], b = S.bst[tid * 4 + e][1];
           d[0] = make_uint4(id, a.x, a.y, a.z);
           d[1] = make_uint4(a.w, b.x, b.y, b.z);
           if (P.desc_words == 16) d[2] = make_uint4(b.w, 0u, 0u, 0u);
