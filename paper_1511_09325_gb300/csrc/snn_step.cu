@@ -50,6 +50,7 @@ constexpr int kUpdateSubs = kBatchThreads / kUpdateThreads;
 constexpr int kDepthF32 = 2;     // rounds of 32-byte sectors in flight per lane, F32W
 constexpr int kDepthF16 = 2;     // the same, F16W
 constexpr int kTile = kUpdateThreads * 4;    // neurons per update tile
+constexpr int kStageSpikes = 128;            // spikers per tile whose bucket ends are staged
 constexpr int kTileCols = kTile / 2 + 2;     // columns a tile can touch (npc >= 2)
 constexpr int kBatchItems = 32;              // items per warp batch (one per lane)
 
@@ -157,10 +158,12 @@ struct UpdateSmem {
   unsigned long long rc, spk;
   unsigned long long synw[kUpdateThreads / 32];  // synaptic events per warp
   unsigned ksum[kUpdateThreads / 32];
-  // bucket ends of the tile's spikers, copied asynchronously as soon as the
-  // spike is known (slot 4 tid + e: neuron e of the thread's quad), so the
-  // load's latency overlaps the tile's count bookkeeping
-  uint4 bst[kTile][2];
+  // bucket ends of the tile's first kStageSpikes spikers, copied
+  // asynchronously as soon as the spike is known, so the load's latency
+  // overlaps the tile's count bookkeeping (later spikers load theirs when
+  // the descriptor is written)
+  unsigned nbst;
+  uint4 bst[kStageSpikes][2];
 };
 
 // Update body vb of vgrid for step t, run by kUpdateThreads threads (thread
@@ -237,6 +240,7 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
       S.tpop[k][0] = 0u;
       S.tpop[k][1] = 0u;
     }
+    if (tid == 0) S.nbst = 0u;
     body_sync(bar);
 
     const long long q = tile * kUpdateThreads + tid;
@@ -289,16 +293,22 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
         }
       }
       if (P.desc != nullptr) {
+        // stage the bucket ends of the first kStageSpikes spikers (slot in
+        // bits 16..23 of the rank; 255: none)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           if (scol[e] >= 0) {
-            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&S.bst[tid * 4 + e][0]);
-            const uint4* src = reinterpret_cast<const uint4*>(P.bend + (i0 + e) * kBendStride);
-            asm volatile(
-                "cp.async.cg.shared.global [%0], [%1], 16;\n\t"
-                "cp.async.cg.shared.global [%2], [%3], 16;" ::"r"(dst),
-                "l"(src), "r"(dst + 16u), "l"(src + 1)
-                : "memory");
+            const unsigned bs = atomicAdd(&S.nbst, 1u);
+            if (bs < (unsigned)kStageSpikes) {
+              const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&S.bst[bs][0]);
+              const uint4* src = reinterpret_cast<const uint4*>(P.bend + (i0 + e) * kBendStride);
+              asm volatile(
+                  "cp.async.cg.shared.global [%0], [%1], 16;\n\t"
+                  "cp.async.cg.shared.global [%2], [%3], 16;" ::"r"(dst),
+                  "l"(src), "r"(dst + 16u), "l"(src + 1)
+                  : "memory");
+            }
+            rank[e] |= (bs < (unsigned)kStageSpikes ? bs : 255u) << 16;
           }
         }
       }
@@ -345,14 +355,23 @@ __device__ __forceinline__ void update_body(const StepParams& P, long long t, in
     for (int e = 0; e < 4; ++e) {
       if (scol[e] >= 0) {
         const int k = scol[e];
-        const unsigned r = rank[e] & 0x7FFFFFFFu;
+        const unsigned r = rank[e] & 0xFFFFu;
         const unsigned off = (rank[e] & 0x80000000u) ? S.tpop[k][0] + r : r;
         const uint32_t id = (uint32_t)(i0 + e);
         const long long pos = P.ccnt != nullptr ? S.lbase[k] + off : S.cbase + S.tpos[k] + off;
         if (P.desc != nullptr) {
-          // descriptor: id, then the bucket ends of the spiker's row (staged)
+          // descriptor: id, then the bucket ends of the spiker's row
           uint4* d = reinterpret_cast<uint4*>(P.desc + ((long long)slot * P.N + pos) * P.desc_words);
-          const uint4 a = S.bst[tid * 4 + e][0], b = S.bst[tid * 4 + e][1];
+          const unsigned bs = (rank[e] >> 16) & 0xFFu;
+          uint4 a, b;
+          if (bs != 255u) {
+            a = S.bst[bs][0];
+            b = S.bst[bs][1];
+          } else {
+            const uint4* be = reinterpret_cast<const uint4*>(P.bend + (long long)id * kBendStride);
+            a = be[0];
+            b = be[1];
+          }
           d[0] = make_uint4(id, a.x, a.y, a.z);
           d[1] = make_uint4(a.w, b.x, b.y, b.z);
           if (P.desc_words == 16) d[2] = make_uint4(b.w, 0u, 0u, 0u);
