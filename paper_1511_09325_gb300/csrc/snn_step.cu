@@ -757,11 +757,12 @@ __device__ __forceinline__ void stream_items(const StepParams& P, const Item& it
 // multiple of 4) into the accumulator with one bulk asynchronous reduction
 // (cp.reduce.async.bulk .add.s32, element-wise atomic in L2) per column,
 // issued by threads 0 .. slots - 1.  The shared-memory writes of every thread
-// are made visible to the bulk copies (async-proxy fence, then a barrier);
-// the issuing threads wait until their copies have read the window, and a
-// last barrier hands the window back to the block.
-__device__ __forceinline__ void flush_window_bulk(const DeliverSmem& S, uint32_t win_s, int slots,
-                                                  int npc, int32_t* acc, int tid) {
+// are made visible to the bulk copies (async-proxy fence, then a barrier).
+// The copies run while the block sets up its next part; flush_wait (the
+// issuing threads wait until their copies have read the window, then a
+// barrier) must come before anything writes the window area again.
+__device__ __forceinline__ void flush_issue(const DeliverSmem& S, uint32_t win_s, int slots, int npc,
+                                            int32_t* acc, int tid) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   if (tid < slots) {
@@ -770,11 +771,13 @@ __device__ __forceinline__ void flush_window_bulk(const DeliverSmem& S, uint32_t
     int32_t* dst = acc + S.wbase[tid];
     asm volatile(
         "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.s32 [%0], [%1], %2;\n\t"
-        "cp.async.bulk.commit_group;\n\t"
-        "cp.async.bulk.wait_group.read 0;" ::"l"(dst),
+        "cp.async.bulk.commit_group;" ::"l"(dst),
         "r"(src), "r"(bytes)
         : "memory");
   }
+}
+__device__ __forceinline__ void flush_wait(int tid, int slots) {
+  if (tid < slots) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
   __syncthreads();
 }
 
@@ -914,6 +917,7 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
   unsigned long long pbase = S.p0;  // items before the tile part's first column
   unsigned long long covered = 0ull;  // items of the range found in the spike lists
   bool win_zero = false;              // the window has been cleared in this body
+  int fl_slots = 0;                   // threads whose window flush may still read the window
   for (int v = v0; v <= v1;) {
     // the part's extent: one tile whose items in the range reach the window
     // threshold (delivered through the window), else a run of consecutive
@@ -986,6 +990,10 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
     }
     unsigned long long ptotal = 0ull;
     unsigned run = (unsigned)block_scan(sum, S, &ptotal);
+    if (!windowed && fl_slots) {  // this part's tables go into the window area
+      flush_wait(tid, fl_slots);
+      fl_slots = 0;
+    }
 #pragma unroll
     for (int q = 0; q < kEpt; ++q) {
       const int e = tid * ept + q;
@@ -999,6 +1007,10 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
     const unsigned b = hi > pbase ? (unsigned)min(hi - pbase, ptotal) : 0u;
     covered += b > a ? b - a : 0u;
     const WinGeo wg = win_geo(P, g, windowed);
+    if (windowed && fl_slots) {
+      flush_wait(tid, fl_slots);
+      fl_slots = 0;
+    }
     if (windowed && !win_zero) {
       for (int i = tid; i < (P.win_cap >> 2); i += NT) reinterpret_cast<int4*>(win)[i] = make_int4(0, 0, 0, 0);
       win_zero = true;
@@ -1049,19 +1061,18 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
       }
     }
     const uint32_t wlen = (uint32_t)(wg.ww * wg.wh) * (uint32_t)P.npc;
+    __syncthreads();  // every warp is done with the part
     if ((P.npc & 3) == 0) {
       // bulk flush: each window slot (one column, n_per_col words, 16-byte
       // aligned in both memories) is added into the accumulator by one
-      // asynchronous bulk reduction; the window is cleared once the bulk
-      // copies have read it (unless no part follows in this body)
-      flush_window_bulk(S, win_s, wg.ww * wg.wh, P.npc, P.acc, tid);
-      if (ve + 1 <= v1) {
-        for (uint32_t i = tid; i < (wlen >> 2); i += NT) reinterpret_cast<int4*>(win)[i] = make_int4(0, 0, 0, 0);
-      } else {
+      // asynchronous bulk reduction, which overlaps the next part's set-up;
+      // the window is cleared again before a later part uses it
+      if (windowed) {
+        flush_issue(S, win_s, wg.ww * wg.wh, P.npc, P.acc, tid);
+        fl_slots = wg.ww * wg.wh;
         win_zero = false;
       }
     } else {
-      __syncthreads();
       // flush the window with coalesced reductions, leaving it zeroed: word
       // m is neuron l of slot s; (s, l) advance with m
       uint32_t fs = div_by((uint32_t)tid, (uint32_t)P.npc, P.npc_m);
@@ -1084,6 +1095,11 @@ __device__ __forceinline__ void deliver_body(const StepParams& P, long long t, i
     v = ve + 1;
     __syncthreads();
   }
+  // the body's bulk reductions must have been performed (not only have read
+  // the window) before it ends: the batch kernel's next phase reads the
+  // accumulator after a grid barrier
+  if (tid < (kMaxTile + 2) * (kMaxTile + 2)) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  __syncthreads();
   // every item of the range must have been found in the spike lists
   if (tid == 0 && covered != hi - lo) set_status(P, kStatusCounts);
 }
