@@ -368,8 +368,9 @@ int snn_batch_step(snn_batch* batch, int64_t n_steps);
 snn_net* snn_batch_net(snn_batch* batch, int k);
 
 /*
- * snn_batch_tune -- pick the fastest delivery schedule for this batch (16-byte
- * chunks in flight per lane: 4 or 2; shared-memory windows: on or off), then
+ * snn_batch_tune -- pick the fastest delivery schedule for this batch (rounds
+ * of 32-byte sectors in flight per lane: 2 or 1, i.e. 4 or 2 chunks of 16
+ * bytes; shared-memory windows: on or off), then
  * the fastest delivery density (8, 4, 2 or 1 virtual delivery blocks per
  * member column, at most the member's standalone grid), each by timing two
  * interleaved rounds of steps_per_trial steps of every candidate (16 trials
