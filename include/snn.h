@@ -280,6 +280,16 @@ int snn_shard_deliver(snn_net* net, const int32_t* ids, int64_t n, int32_t ids_o
 int snn_shard_info(snn_net* net, int32_t* geo, int n);
 
 /*
+ * snn_shard_geometry -- the geometry snn_build_shard gives the shard of tile
+ * (x0, y0, w, h) of a grid_w x grid_h grid with the given stencil_radius
+ * (1..3), in the layout of snn_shard_info, without building anything (host
+ * only, no device call).  SNN_EINVAL for a grid outside 1..16383 columns a
+ * side, a tile outside the grid, a radius outside 1..3 or a NULL geo.
+ */
+int snn_shard_geometry(int grid_w, int grid_h, int x0, int y0, int w, int h, int stencil_radius,
+                       int32_t* geo, int n);
+
+/*
  * snn_step_profiled -- like snn_step, but each step's kernels are launched
  * one by one with CUDA events around each on the net's stream.  Writes the
  * summed device milliseconds of the neuron-update and delivery kernels and,

@@ -641,6 +641,67 @@ int snn_build(int grid_w, int grid_h, const snn_neuron_params* neuron,
                    kMinItems, kPartCols, out);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Local grid of the shard of tile (x0, y0, w, h): the tile and a halo of R
+// columns on each side, or the whole grid side where the two would meet.
+// *ew, *eh receive the local grid's size.
+int shard_geometry(int grid_w, int grid_h, int x0, int y0, int w, int h, int R, ShardGeo* g, int* ew,
+                   int* eh) {
+  if (grid_w < 1 || grid_h < 1 || grid_w > kMaxGridSide || grid_h > kMaxGridSide)
+    return fail(nullptr, SNN_EINVAL, "grid_w and grid_h must be in 1..16383");
+  if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || x0 > grid_w - w || y0 > grid_h - h)
+    return fail(nullptr, SNN_EINVAL, "the shard's tile must lie inside the grid");
+  if (R < 1 || R > 3) return fail(nullptr, SNN_EINVAL, "stencil_radius must be 1..3");
+  *g = ShardGeo{};
+  g->on = 1;
+  g->GW = grid_w;
+  g->GH = grid_h;
+  g->tw = w;
+  g->th = h;
+  *ew = grid_w;
+  *eh = grid_h;
+  if (w + 2 * R < grid_w) {
+    *ew = w + 2 * R;
+    g->ex0 = (x0 - R + grid_w) % grid_w;
+    g->tx0 = R;
+  } else {
+    g->ex0 = 0;
+    g->tx0 = x0;
+  }
+  if (h + 2 * R < grid_h) {
+    *eh = h + 2 * R;
+    g->ey0 = (y0 - R + grid_h) % grid_h;
+    g->ty0 = R;
+  } else {
+    g->ey0 = 0;
+    g->ty0 = y0;
+  }
+  return SNN_OK;
+}
+
+void geometry_words(const ShardGeo& g, int ew, int eh, int32_t* geo, int n) {
+  const int32_t v[10] = {g.GW, g.GH, ew, eh, g.ex0, g.ey0, g.tx0, g.ty0, g.tw, g.th};
+  for (int i = 0; i < n && i < 10; ++i) geo[i] = v[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+int snn_shard_geometry(int grid_w, int grid_h, int x0, int y0, int w, int h, int stencil_radius,
+                       int32_t* geo, int n) {
+  if (!geo) return fail(nullptr, SNN_EINVAL, "geo is NULL");
+  ShardGeo g{};
+  int ew = 0, eh = 0;
+  const int rc = shard_geometry(grid_w, grid_h, x0, y0, w, h, stencil_radius, &g, &ew, &eh);
+  if (rc != SNN_OK) return rc;
+  geometry_words(g, ew, eh, geo, n);
+  return SNN_OK;
+}
+
 int snn_build_shard(int grid_w, int grid_h, int x0, int y0, int w, int h,
                     const snn_neuron_params* neuron, const snn_synapse_params* synapse,
                     uint64_t seed, int precision, void* cuda_stream, snn_net** out) {
@@ -649,38 +710,14 @@ int snn_build_shard(int grid_w, int grid_h, int x0, int y0, int w, int h,
   std::string why;
   const int vrc = validate(grid_w, grid_h, neuron, synapse, precision, &why);
   if (vrc != SNN_OK) return fail(nullptr, vrc, why);
-  if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || x0 + w > grid_w || y0 + h > grid_h)
-    return fail(nullptr, SNN_EINVAL, "the shard's tile must lie inside the grid");
   if (synapse->connectivity != SNN_CONN_FIXED)
     return fail(nullptr, SNN_EINVAL, "shards support SNN_CONN_FIXED only");
   if (neuron->n_per_col % 4 != 0)
     return fail(nullptr, SNN_EINVAL, "shards need n_per_col to be a multiple of 4");
-  // local grid: the tile and a halo as wide as the stencil, or the whole side
-  // where the two would meet
-  const int R = synapse->stencil_radius;
   ShardGeo g{};
-  g.on = 1;
-  g.GW = grid_w;
-  g.GH = grid_h;
-  g.tw = w;
-  g.th = h;
-  int ew = grid_w, eh = grid_h;
-  if (w + 2 * R < grid_w) {
-    ew = w + 2 * R;
-    g.ex0 = (x0 - R + grid_w) % grid_w;
-    g.tx0 = R;
-  } else {
-    g.ex0 = 0;
-    g.tx0 = x0;
-  }
-  if (h + 2 * R < grid_h) {
-    eh = h + 2 * R;
-    g.ey0 = (y0 - R + grid_h) % grid_h;
-    g.ty0 = R;
-  } else {
-    g.ey0 = 0;
-    g.ty0 = y0;
-  }
+  int ew = 0, eh = 0;
+  const int grc = shard_geometry(grid_w, grid_h, x0, y0, w, h, synapse->stencil_radius, &g, &ew, &eh);
+  if (grc != SNN_OK) return grc;
   return build_net(ew, eh, neuron, synapse, seed, precision, cuda_stream, kWindowBudget, kMinItems,
                    kPartCols, out, &g);
 }
@@ -734,9 +771,7 @@ int snn_shard_deliver(snn_net* net, const int32_t* ids, int64_t n, int32_t ids_o
 int snn_shard_info(snn_net* net, int32_t* geo, int n) {
   if (!net || !geo) return fail(net, SNN_EINVAL, "null argument");
   if (!net->sg.on) return fail(net, SNN_ESTATE, "not a shard");
-  const int32_t v[10] = {net->sg.GW, net->sg.GH, net->W, net->H, net->sg.ex0, net->sg.ey0,
-                         net->sg.tx0, net->sg.ty0, net->sg.tw, net->sg.th};
-  for (int i = 0; i < n && i < 10; ++i) geo[i] = v[i];
+  geometry_words(net->sg, net->W, net->H, geo, n);
   return SNN_OK;
 }
 

@@ -24,6 +24,7 @@ EXPORTS = ("snn_build", "snn_step", "snn_read_spikes", "snn_pending_spikes",
            "snn_read_synapses", "snn_row_lengths", "snn_info", "snn_step_profiled", "snn_update_noalloc",
            "snn_debug_offset_count",
            "snn_build_shard", "snn_shard_update", "snn_shard_deliver", "snn_shard_info",
+           "snn_shard_geometry",
            "snn_batch_build", "snn_batch_step", "snn_batch_net", "snn_batch_tune",
            "snn_batch_set_wait", "snn_batch_last_error", "snn_batch_destroy",
            "snn_grad_build", "snn_grad_run", "snn_grad_last_error", "snn_grad_destroy",
@@ -77,6 +78,7 @@ def load(path=LIB_PATH):
     L.snn_shard_update.argtypes = [vp]
     L.snn_shard_deliver.argtypes = [vp, vp, i64, ctypes.c_int32]
     L.snn_shard_info.argtypes = [vp, vp, i32]
+    L.snn_shard_geometry.argtypes = [i32, i32, i32, i32, i32, i32, i32, vp, i32]
     L.snn_read_spikes.argtypes = [vp, vp, vp, i64, P(i64)]
     L.snn_pending_spikes.argtypes = [vp, P(i64)]
     L.snn_set_record_capacity.argtypes = [vp, i64]
@@ -197,11 +199,40 @@ def snn_shard_deliver(handle, ids):
     _check(rc, handle)
 
 
+_GEO_KEYS = ("grid_w", "grid_h", "local_w", "local_h", "ex0", "ey0", "tx0", "ty0", "w", "h")
+
+
 def snn_shard_info(handle):
     g = np.zeros(10, np.int32)
     _check(load().snn_shard_info(handle, _p(g), 10), handle)
-    keys = ("grid_w", "grid_h", "local_w", "local_h", "ex0", "ey0", "tx0", "ty0", "w", "h")
-    return {k: int(v) for k, v in zip(keys, g)}
+    return {k: int(v) for k, v in zip(_GEO_KEYS, g)}
+
+
+def snn_shard_geometry(grid_w, grid_h, tile, stencil_radius):
+    """The geometry of the shard of `tile` = (x0, y0, w, h) (host only)."""
+    x0, y0, w, h = tile
+    g = np.zeros(10, np.int32)
+    _check(load().snn_shard_geometry(int(grid_w), int(grid_h), int(x0), int(y0), int(w), int(h),
+                                     int(stencil_radius), _p(g), 10), None)
+    return {k: int(v) for k, v in zip(_GEO_KEYS, g)}
+
+
+def shard_local_to_global(geo, npc, local_ids):
+    """Global neuron indices of a shard's local neuron indices."""
+    j = np.asarray(local_ids, np.int64)
+    c, l = j // npc, j % npc
+    ly, lx = c // geo["local_w"], c % geo["local_w"]
+    gx = (geo["ex0"] + lx) % geo["grid_w"]
+    gy = (geo["ey0"] + ly) % geo["grid_h"]
+    return (gy * geo["grid_w"] + gx) * npc + l
+
+
+def shard_tile_neurons(geo, npc):
+    """Local indices of a shard's tile neurons: tile rows, then columns, then l."""
+    ly, lx = np.meshgrid(np.arange(geo["ty0"], geo["ty0"] + geo["h"]),
+                         np.arange(geo["tx0"], geo["tx0"] + geo["w"]), indexing="ij")
+    c = (ly * geo["local_w"] + lx).reshape(-1, 1)
+    return (c * npc + np.arange(npc)).reshape(-1)
 
 
 def snn_pending_spikes(handle):
@@ -630,21 +661,11 @@ class Shard:
 
     def local_to_global(self, local_ids):
         """Global neuron indices of local neuron indices."""
-        g = self.geo
-        j = np.asarray(local_ids, np.int64)
-        c, l = j // self.npc, j % self.npc
-        ly, lx = c // g["local_w"], c % g["local_w"]
-        gx = (g["ex0"] + lx) % g["grid_w"]
-        gy = (g["ey0"] + ly) % g["grid_h"]
-        return (gy * g["grid_w"] + gx) * self.npc + l
+        return shard_local_to_global(self.geo, self.npc, local_ids)
 
     def tile_local_neurons(self):
         """Local indices of the tile's neurons, tile row-major, then l."""
-        g = self.geo
-        ly, lx = np.meshgrid(np.arange(g["ty0"], g["ty0"] + g["h"]),
-                             np.arange(g["tx0"], g["tx0"] + g["w"]), indexing="ij")
-        c = (ly * g["local_w"] + lx).reshape(-1, 1)
-        return (c * self.npc + np.arange(self.npc)).reshape(-1)
+        return shard_tile_neurons(self.geo, self.npc)
 
     def update(self):
         snn_shard_update(self.handle)
